@@ -1,0 +1,311 @@
+"""Benchmark of the multispin Kob-Andersen sweep on one or more GB300s.
+
+Workload (one bench step): the periodic cubic lattice d=3, L=128
+(2,097,152 sites), z=6, m=3, 256 replicas (4 uint64 words per site), at the
+three densities rho = 0.80, 0.85, 0.88 (one context each, Philox seed 1):
+S sweeps of every context followed by one device-side observation.  The
+state of one context is 192 MiB (n, n0, p); the three together, 576 MiB,
+exceed the 126 MB L2, so no L2 flush is needed between steps.
+
+Metric: attempted KA moves per second counted per site x replica
+(N * R * sweeps / time), whole job.  Printed as one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--sweeps S] [--impl native|reference]
+
+--impl reference times the CPU oracle (the serial restatement of the paper
+used by the tests) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+D, L, M, R, SEED = 3, 128, 3, 256, 1
+RHOS = (0.80, 0.85, 0.88)
+N_SITES = L ** D
+WORDS = R // 64
+BYTES_PER_SITE_WORD_SWEEP = 32  # read + write of n and p, 8 bytes each
+METRIC = "attempted KA moves/s (site x replica)"
+UNIT = "site-replica moves/s"
+WORKLOAD = ("cubic d=3 L=128 z=6 m=3, 256 replicas, rho in {0.80,0.85,0.88}, "
+            "Philox seed 1, periodic")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(n_rep: int, sweeps: int, rho: float = RHOS[0]):
+    """Time the oracle on n_rep replicas of the workload (initial state untimed)."""
+    import oracle as O
+
+    topo = O.cubic(D, L)
+    st = O.init(topo.N, n_rep, SEED, rho)
+    t0 = time.perf_counter()
+    O.sweeps(topo, M, st, SEED, sweeps)
+    dt = time.perf_counter() - t0
+    return N_SITES * n_rep * sweeps / dt, dt
+
+
+def run_reference(args, rank: int) -> None:
+    if rank != 0:
+        return
+    import oracle as O
+
+    topo = O.cubic(D, L)
+    n_rep = 4
+    st = O.init(topo.N, n_rep, SEED, RHOS[0])
+    for _ in range(args.warmup):
+        O.sweeps(topo, M, st, SEED, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.sweeps(topo, M, st, SEED, 1)
+    dt = time.perf_counter() - t0
+    value = N_SITES * n_rep * args.steps / dt
+    sample = (f"oracle, 1 thread: L=128 d=3 m=3 rho=0.80, {n_rep} of 256 replicas, "
+              f"1 sweep per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "L": L, "d": D, "m": M, "replicas": R, "rho": list(RHOS)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args, rank: int, world: int) -> None:
+    import torch
+
+    import paper_1710_05155_gb300 as K
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+    stream = torch.cuda.current_stream(dev)
+    S = args.sweeps
+
+    # one context per density; weak scaling: every rank runs its own replicas
+    sims = []
+    for k, rho in enumerate(RHOS):
+        sim = K.Simulation(topo=K.KA_CUBIC, d=D, L=L, m=M, replicas=R, device=dev, stream=stream)
+        sim.init(SEED + 1000 * rank, rho)
+        sims.append(sim)
+    counts_dev = [torch.zeros((R, 4), dtype=torch.int64, device=f"cuda:{dev}") for _ in sims]
+    P = sims[0].info["words"] // 2 if sims[0].info["words"] % 2 == 0 else sims[0].info["words"]
+    groups = 2 * D
+    launches_per_step = len(sims) * (P * S * groups + 1)
+
+    def step():
+        for sim, cd in zip(sims, counts_dev):
+            K.ka_sweep(sim.ctx, S)
+            K.ka_observe_device(sim.ctx, cd.data_ptr())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    moves = N_SITES * R * S * len(sims) * args.steps * world
+    value = moves / (ms / 1000.0)
+
+    # kernel duration of the pencil kernel, CUDA events around every launch
+    K.ka_profile_enable(sims[0].ctx, True)
+    K.ka_sweep(sims[0].ctx, S)
+    kms, nl = K.ka_profile_read(sims[0].ctx)
+    K.ka_profile_enable(sims[0].ctx, False)
+    avg_launch_ms = kms / max(nl, 1)
+    V = 2 if WORDS % 2 == 0 else 1
+    bytes_per_launch = BYTES_PER_SITE_WORD_SWEEP * N_SITES * V / groups
+    achieved = bytes_per_launch / (avg_launch_ms / 1000.0) / 1e9
+    peak, peak_kind = _peaks()
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get("k_cubic_group_bytes_per_launch")
+    except Exception:
+        pass
+
+    # end to end through the C ABI: initial state from pinned host memory,
+    # S sweeps, counts back to the host, for every context
+    host_init = []
+    for sim in sims:
+        n, n0, p = sim.get_state()
+        pinned = []
+        for a in (n, n0, p):
+            t = torch.empty(a.shape, dtype=torch.int64, pin_memory=True)
+            t.numpy().view(np.uint64)[...] = a
+            pinned.append(t.numpy().view(np.uint64))
+        host_init.append(pinned)
+    out = [np.zeros((R, 4), np.int64) for _ in sims]
+    e2e_steps = max(2, min(args.steps, 5))
+
+    def e2e_step():
+        for sim, hs, o in zip(sims, host_init, out):
+            K.ka_set_state(sim.ctx, hs[0], hs[1], hs[2], 0, SEED)
+            K.ka_sweep(sim.ctx, S)
+            K.ka_observe(sim.ctx, o)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = N_SITES * R * S * len(sims) * e2e_steps * world / e2e_s
+    h2d = len(sims) * 3 * WORDS * N_SITES * 8
+    d2h = len(sims) * R * 4 * 8
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            n_rep, sw = 8, 2
+            v, dt = oracle_sample(n_rep, sw)
+            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"L=128 d=3 m=3 rho=0.80, {n_rep} of 256 replicas, {sw} sweeps "
+                             f"after an untimed init ({dt:.1f} s)"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "L": L, "d": D, "m": M, "replicas": R,
+                       "rho": list(RHOS), "sweeps_per_step": S, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (576 MiB of state per GPU)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_cubic_group", "peak_kind": peak_kind,
+                         "avg_launch_us": 1000.0 * avg_launch_ms,
+                         "bytes_per_launch": bytes_per_launch},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    for sim in sims:
+        sim.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--sweeps", type=int, default=100, help="sweeps per context per step")
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_native(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

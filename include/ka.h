@@ -1,0 +1,200 @@
+/*
+ * ka.h -- C ABI of the GB300 multispin Kob-Andersen library.
+ *
+ * The library runs the Kob-Andersen kinetically constrained lattice gas of
+ * Boccagna, "A Multispin Algorithm for the Kob-Andersen Stochastic Dynamics
+ * on Regular Lattices" (arXiv 1710.05155) with multispin coding (section 3.1):
+ * the occupation of one site in R independent replicas is stored as R/64
+ * uint64 words, one bit per replica.  Replica r lives in word r / 64, bit
+ * r % 64.
+ *
+ * Dynamics (section 2.1, rules (a)-(c); section 3.2).  A sweep runs a fixed
+ * sequence of bond classes.  Each class is a strong matching (no two bonds
+ * share a site or are joined by an edge), so its bonds are independent.  On a
+ * bond (i, j) every replica exchanges n_i and n_j iff
+ *   - exactly one of i, j is occupied                          (rule (a)),
+ *   - the occupied site has at most m occupied neighbours      (rule (b)),
+ *   - the empty site has at most m + 1 occupied neighbours     (rule (c)),
+ *   - the replica's random gate bit for this attempt is 1.
+ * Equivalently: at most m of the z-1 other neighbours of i are occupied, and
+ * at most m of the z-1 other neighbours of j.  An exchange clears the
+ * persistence bit of both sites.
+ *
+ * Random gates.  Philox4x32-10 (Salmon et al., SC'11), key = (seed low 32,
+ * seed high 32).  The gate word of word w of bond b in class c at sweep t is
+ * half (w mod 2) of the block at counter (t, c, b, w / 2); half 0 is
+ * x0 | x1 << 32, half 1 is x2 | x3 << 32.  Bond b is the base site index on
+ * cubic lattices and the edge id on graphs.
+ *
+ * Cubic schedule (d-dimensional periodic lattice, L % 4 == 0, site index
+ * i = sum_k x_k L^k).  Class c = (2 mu + p) * 4 + a, for mu < d, p in {0, 1}
+ * (only p = 0 when d = 1) and a < 4, holds the bonds (x, x + e_mu) with
+ * x_mu = a mod 4 and sum_{nu != mu} x_nu = p mod 2.  Classes run in
+ * ascending c.
+ *
+ * Graph schedule (random regular graphs and caller graphs).  Edges (u < v)
+ * sorted lexicographically get ids 0..E-1; a greedy strong edge colouring in
+ * id order gives the classes, run in ascending colour.
+ *
+ * Random regular graphs: configuration model (section 2.1, Bollobas); stubs
+ * are shuffled by Fisher-Yates with Lemire's bounded integers from Philox
+ * counter (attempt, 0xFFFFFFFE, k, draw) keyed by graph_seed, paired
+ * (2q, 2q+1), and the whole attempt is rejected on any self-loop or
+ * multi-edge.  This samples simple z-regular graphs uniformly.
+ *
+ * Initial state (section 3.1: draw a configuration at density rho at
+ * random): K = round-half-away(rho N) particles per replica at the K sites
+ * with the smallest (key, site), key = half (r mod 2) of the Philox block at
+ * counter (r / 2, 0xFFFFFFFF, site, 0) keyed by seed.  n0 = n, p = all ones.
+ *
+ * Observables (section 2.2 overlap q_i = n_i(t) n_i(0); section 3.3 popcounts):
+ * per replica, int64 [R][4] = { sum n, sum n & n0, sum n0 & p, sum p }.
+ * C(t) = mean_r (overlap_r - N rho^2) / (N rho (1 - rho)) with rho = K / N.
+ *
+ * Errors.  Every entry point returns a ka_status; no exception crosses the
+ * ABI.  Kernel faults surface as KA_ECUDA at the next call that synchronises
+ * (ka_observe, ka_get_state, ka_sync, ka_destroy).  ka_last_error gives a
+ * message.  A context is not thread-safe; distinct contexts are independent.
+ * All device work of a context is issued on its stream, in call order.
+ */
+#ifndef KA_H
+#define KA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KA_OK = 0,
+    KA_EINVAL = 1,   /* bad argument or unsupported parameter set */
+    KA_ENOMEM = 2,   /* device or host allocation failed, or buffer too small */
+    KA_ECUDA = 3,    /* CUDA runtime or kernel error */
+    KA_ETIMEOUT = 4, /* a bounded device wait ran out */
+    KA_EBUSY = 5,    /* resource budget exhausted (admission refused) */
+    KA_ESTATE = 6    /* call out of order (e.g. sweep before init) */
+} ka_status;
+
+typedef enum {
+    KA_CUBIC = 0, /* periodic d-dimensional cubic lattice, z = 2d */
+    KA_RRG = 1,   /* random z-regular graph built from graph_seed */
+    KA_GRAPH = 2  /* caller-supplied simple z-regular graph (nbr) */
+} ka_topology;
+
+/* flags */
+#define KA_FLAG_GENERIC 1 /* cubic lattices: use the edge-gather kernel, not the pencil kernel */
+
+typedef struct {
+    int32_t topo;        /* ka_topology */
+    int32_t d;           /* cubic: 1 <= d <= 4 */
+    int32_t L;           /* cubic: L >= 4, L % 4 == 0, L^d < 2^31 */
+    int32_t z;           /* graphs: 1 <= z <= 8, z < N (cubic: ignored, z = 2d) */
+    int64_t N;           /* graphs: number of vertices, N z even, N z < 2^32 (cubic: ignored) */
+    int32_t m;           /* activation number, 0 <= m <= z - 1 (section 2.1) */
+    int32_t replicas;    /* R, a positive multiple of 64 */
+    uint64_t graph_seed; /* KA_RRG */
+    const int32_t *nbr;  /* KA_GRAPH: host array [N][z], copied at create; else NULL */
+    void *stream;        /* cudaStream_t for all work of the context; NULL = legacy default */
+    int32_t device;      /* CUDA device ordinal */
+    int32_t flags;       /* KA_FLAG_* */
+} ka_params;
+
+typedef struct ka_ctx ka_ctx;
+
+typedef struct {
+    int64_t N;          /* sites */
+    int32_t z;          /* neighbours per site */
+    int32_t m;          /* activation number */
+    int32_t replicas;   /* R */
+    int32_t words;      /* R / 64 */
+    int64_t nclass;     /* bond classes per sweep */
+    int64_t nbonds;     /* bonds per sweep = N z / 2 */
+    int64_t sweep;      /* sweeps completed since init (or set_state) */
+    int64_t K;          /* particles per replica at the last init (-1 if none) */
+    uint64_t seed;      /* dynamics seed */
+    int32_t kernel;     /* 0 = cubic pencil kernel, 1 = edge-gather kernel */
+    int32_t rrg_attempts; /* configuration-model attempts (KA_RRG) */
+    size_t device_bytes;  /* device memory the context uses */
+} ka_info_t;
+
+/* Device bytes ka_create_in needs for these parameters. */
+ka_status ka_required_bytes(const ka_params *params, size_t *bytes);
+
+/* Create a context; the library allocates its device memory with cudaMalloc
+ * and frees it in ka_destroy.  Builds the graph and its bond classes on the
+ * host (KA_RRG, KA_GRAPH) and uploads them.  *out is NULL on failure. */
+ka_status ka_create(const ka_params *params, ka_ctx **out);
+
+/* As ka_create, but all device memory is carved from the caller's buffer
+ * (at least ka_required_bytes, 256-byte aligned).  The caller keeps
+ * ownership and must keep the buffer alive until ka_destroy. */
+ka_status ka_create_in(const ka_params *params, void *device_buffer, size_t bytes, ka_ctx **out);
+
+/* Initial state at density rho in [0, 1] with dynamics seed `seed`; resets
+ * the sweep counter to 0.  Asynchronous on the context stream. */
+ka_status ka_init(ka_ctx *ctx, uint64_t seed, double rho);
+
+/* Run n >= 0 sweeps (every class once, in order).  Asynchronous.  The sweep
+ * counter must stay below 2^32 (it is a Philox counter word). */
+ka_status ka_sweep(ka_ctx *ctx, int64_t n);
+
+/* Observables of the current state into host int64 counts[R][4]; writes the
+ * sweep counter to *sweep_out (may be NULL).  Synchronises the stream. */
+ka_status ka_observe(ka_ctx *ctx, int64_t *sweep_out, int64_t *counts);
+
+/* Observables into a device buffer int64 [R][4] (overwritten), no
+ * synchronisation. */
+ka_status ka_observe_device(ka_ctx *ctx, int64_t *counts_device);
+
+/* Copy the state to host arrays in canonical layout [R/64][N] uint64 each
+ * (word-plane major).  Any pointer may be NULL.  Synchronises. */
+ka_status ka_get_state(ka_ctx *ctx, uint64_t *n, uint64_t *n0, uint64_t *p);
+
+/* Load a state from host arrays in canonical layout; sets the sweep counter.
+ * n, n0 and p are all required.  Synchronises. */
+ka_status ka_set_state(ka_ctx *ctx, const uint64_t *n, const uint64_t *n0, const uint64_t *p,
+                       int64_t sweep, uint64_t seed);
+
+/* Wait for all work of the context; reports deferred kernel errors. */
+ka_status ka_sync(ka_ctx *ctx);
+
+/* Context description. */
+ka_status ka_info(const ka_ctx *ctx, ka_info_t *out);
+
+/* Host copies of the topology: nbr [N][z], class_off [nclass+1],
+ * bu / bv / bid [nbonds] (bonds grouped by class, in class order).  Any
+ * pointer may be NULL. */
+ka_status ka_graph_tables(const ka_ctx *ctx, int32_t *nbr, int64_t *class_off, int32_t *bu,
+                          int32_t *bv, int64_t *bid);
+
+/* Host only (no device, no context): build the topology of `params` as
+ * ka_create would and report its size; copy the tables into the non-NULL
+ * buffers.  Capacities: nbr N*z, class_off nbonds+1 (the class count of a
+ * random graph is known only after colouring), bu / bv / bid nbonds. */
+ka_status ka_build_topology(const ka_params *params, int64_t *nclass, int64_t *nbonds,
+                            int32_t *nbr,
+                      int64_t *class_off, int32_t *bu, int32_t *bv, int64_t *bid);
+
+/* Kernel timing for roofline reports.  When enabled, ka_sweep brackets
+ * every sweep-kernel launch with CUDA events on the context stream;
+ * ka_profile_read synchronises and returns the summed kernel time and the
+ * number of launches since the last read. */
+ka_status ka_profile_enable(ka_ctx *ctx, int32_t enable);
+ka_status ka_profile_read(ka_ctx *ctx, double *kernel_ms, int64_t *launches);
+
+/* Destroy a context (NULL is fine).  Synchronises; returns a deferred
+ * kernel error if one is pending. */
+ka_status ka_destroy(ka_ctx *ctx);
+
+/* Message of the last failed call on this context (never NULL). */
+const char *ka_last_error(const ka_ctx *ctx);
+
+/* Human-readable name of a status code. */
+const char *ka_status_name(ka_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

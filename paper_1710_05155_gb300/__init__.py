@@ -1,0 +1,311 @@
+"""Python binding of the GB300 multispin Kob-Andersen library (include/ka.h).
+
+A thin ctypes layer over the C ABI: the functions keep the C names and only
+marshal arguments.  Every step of the dynamics runs in the CUDA library; if
+the library cannot be loaded, the calls raise instead of falling back to
+anything else.  PyTorch supplies device memory (``Simulation`` allocates the
+context buffer as a torch tensor) and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+KA_OK, KA_EINVAL, KA_ENOMEM, KA_ECUDA, KA_ETIMEOUT, KA_EBUSY, KA_ESTATE = range(7)
+KA_CUBIC, KA_RRG, KA_GRAPH = 0, 1, 2
+KA_FLAG_GENERIC = 1
+
+_STATUS = {0: "KA_OK", 1: "KA_EINVAL", 2: "KA_ENOMEM", 3: "KA_ECUDA", 4: "KA_ETIMEOUT",
+           5: "KA_EBUSY", 6: "KA_ESTATE"}
+
+
+class KaError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {_STATUS.get(status, status)}" + (f" ({message})" if message else ""))
+
+
+class ka_params(C.Structure):
+    _fields_ = [("topo", C.c_int32), ("d", C.c_int32), ("L", C.c_int32), ("z", C.c_int32),
+                ("N", C.c_int64), ("m", C.c_int32), ("replicas", C.c_int32),
+                ("graph_seed", C.c_uint64), ("nbr", C.POINTER(C.c_int32)),
+                ("stream", C.c_void_p), ("device", C.c_int32), ("flags", C.c_int32)]
+
+
+class ka_info_t(C.Structure):
+    _fields_ = [("N", C.c_int64), ("z", C.c_int32), ("m", C.c_int32), ("replicas", C.c_int32),
+                ("words", C.c_int32), ("nclass", C.c_int64), ("nbonds", C.c_int64),
+                ("sweep", C.c_int64), ("K", C.c_int64), ("seed", C.c_uint64),
+                ("kernel", C.c_int32), ("rrg_attempts", C.c_int32), ("device_bytes", C.c_size_t)]
+
+
+_lib = None
+
+# every symbol include/ka.h declares, with (restype, argtypes)
+_P = C.POINTER
+_SIGS = {
+    "ka_required_bytes": (C.c_int, [_P(ka_params), _P(C.c_size_t)]),
+    "ka_create": (C.c_int, [_P(ka_params), _P(C.c_void_p)]),
+    "ka_create_in": (C.c_int, [_P(ka_params), C.c_void_p, C.c_size_t, _P(C.c_void_p)]),
+    "ka_init": (C.c_int, [C.c_void_p, C.c_uint64, C.c_double]),
+    "ka_sweep": (C.c_int, [C.c_void_p, C.c_int64]),
+    "ka_observe": (C.c_int, [C.c_void_p, _P(C.c_int64), C.c_void_p]),
+    "ka_observe_device": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ka_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ka_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                               C.c_uint64]),
+    "ka_sync": (C.c_int, [C.c_void_p]),
+    "ka_info": (C.c_int, [C.c_void_p, _P(ka_info_t)]),
+    "ka_graph_tables": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p]),
+    "ka_build_topology": (C.c_int, [_P(ka_params), _P(C.c_int64), _P(C.c_int64), C.c_void_p,
+                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ka_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
+    "ka_profile_read": (C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_int64)]),
+    "ka_destroy": (C.c_int, [C.c_void_p]),
+    "ka_last_error": (C.c_char_p, [C.c_void_p]),
+    "ka_status_name": (C.c_char_p, [C.c_int]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library not built: {_build.LIB}")
+    lib = C.CDLL(_build.LIB)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a) -> C.c_void_p:
+    return C.c_void_p(a.ctypes.data) if a is not None else C.c_void_p(0)
+
+
+class Ctx:
+    """An opaque ka_ctx* plus the objects that must outlive it."""
+
+    def __init__(self, handle: int, keep=()):
+        self.handle = C.c_void_p(handle)
+        self._keep = list(keep)
+        self.info = None
+
+    def __bool__(self):
+        return bool(self.handle.value)
+
+
+def _check(status: int, where: str, ctx: Ctx | None = None) -> None:
+    if status != KA_OK:
+        msg = ""
+        if ctx is not None and ctx.handle.value:
+            msg = load().ka_last_error(ctx.handle).decode()
+        raise KaError(status, where, msg)
+
+
+def make_params(topo: int = KA_CUBIC, d: int = 3, L: int = 16, z: int = 0, N: int = 0, m: int = 3,
+                replicas: int = 64, graph_seed: int = 1, nbr=None, stream: int | None = None,
+                device: int = 0, flags: int = 0):
+    p = ka_params()
+    p.topo, p.d, p.L, p.z, p.N, p.m = topo, d, L, z, N, m
+    p.replicas, p.graph_seed, p.device, p.flags = replicas, graph_seed, device, flags
+    keep = None
+    if nbr is not None:
+        keep = np.ascontiguousarray(nbr, np.int32)
+        p.nbr = keep.ctypes.data_as(C.POINTER(C.c_int32))
+    p.stream = stream or 0
+    return p, keep
+
+
+def ka_required_bytes(params: ka_params) -> int:
+    out = C.c_size_t(0)
+    _check(load().ka_required_bytes(C.byref(params), C.byref(out)), "ka_required_bytes")
+    return out.value
+
+
+def ka_create(params: ka_params, keep=()) -> Ctx:
+    h = C.c_void_p(0)
+    _check(load().ka_create(C.byref(params), C.byref(h)), "ka_create")
+    return Ctx(h.value, keep)
+
+
+def ka_create_in(params: ka_params, device_ptr: int, nbytes: int, keep=()) -> Ctx:
+    h = C.c_void_p(0)
+    _check(load().ka_create_in(C.byref(params), C.c_void_p(device_ptr), nbytes, C.byref(h)),
+           "ka_create_in")
+    return Ctx(h.value, keep)
+
+
+def ka_init(ctx: Ctx, seed: int, rho: float) -> None:
+    _check(load().ka_init(ctx.handle, seed, rho), "ka_init", ctx)
+
+
+def ka_sweep(ctx: Ctx, n: int) -> None:
+    _check(load().ka_sweep(ctx.handle, n), "ka_sweep", ctx)
+
+
+def ka_info(ctx: Ctx) -> dict:
+    info = ka_info_t()
+    _check(load().ka_info(ctx.handle, C.byref(info)), "ka_info", ctx)
+    return {k: getattr(info, k) for k, _ in ka_info_t._fields_}
+
+
+def ka_observe(ctx: Ctx, out: np.ndarray | None = None):
+    """(sweep, int64 [R, 4]): particles, overlap, persist_occ, persist_all per replica."""
+    R = ka_info(ctx)["replicas"]
+    if out is None:
+        out = np.zeros((R, 4), np.int64)
+    sweep = C.c_int64(0)
+    _check(load().ka_observe(ctx.handle, C.byref(sweep), _ptr(out)), "ka_observe", ctx)
+    return sweep.value, out
+
+
+def ka_observe_device(ctx: Ctx, counts_device_ptr: int) -> None:
+    _check(load().ka_observe_device(ctx.handle, C.c_void_p(counts_device_ptr)),
+           "ka_observe_device", ctx)
+
+
+def ka_get_state(ctx: Ctx):
+    """Host copies (n, n0, p), each uint64 [R/64, N] in canonical layout."""
+    info = ka_info(ctx)
+    shape = (info["words"], info["N"])
+    n, n0, p = (np.zeros(shape, np.uint64) for _ in range(3))
+    _check(load().ka_get_state(ctx.handle, _ptr(n), _ptr(n0), _ptr(p)), "ka_get_state", ctx)
+    return n, n0, p
+
+
+def ka_set_state(ctx: Ctx, n, n0, p, sweep: int, seed: int) -> None:
+    n, n0, p = (np.ascontiguousarray(x, np.uint64) for x in (n, n0, p))
+    _check(load().ka_set_state(ctx.handle, _ptr(n), _ptr(n0), _ptr(p), sweep, seed),
+           "ka_set_state", ctx)
+
+
+def ka_sync(ctx: Ctx) -> None:
+    _check(load().ka_sync(ctx.handle), "ka_sync", ctx)
+
+
+def ka_graph_tables(ctx: Ctx) -> dict:
+    info = ka_info(ctx)
+    N, z, E, C_ = info["N"], info["z"], info["nbonds"], info["nclass"]
+    t = {"nbr": np.zeros(N * z, np.int32), "class_off": np.zeros(C_ + 1, np.int64),
+         "bu": np.zeros(E, np.int32), "bv": np.zeros(E, np.int32), "bid": np.zeros(E, np.int64)}
+    _check(load().ka_graph_tables(ctx.handle, _ptr(t["nbr"]), _ptr(t["class_off"]), _ptr(t["bu"]),
+                                  _ptr(t["bv"]), _ptr(t["bid"])), "ka_graph_tables", ctx)
+    return t
+
+
+def ka_build_topology(params: ka_params) -> dict:
+    """Host-only topology tables (no device): nbr, class_off, bu, bv, bid."""
+    lib = load()
+    nc, nb = C.c_int64(0), C.c_int64(0)
+    _check(lib.ka_build_topology(C.byref(params), C.byref(nc), C.byref(nb), None, None, None, None,
+                           None), "ka_build_topology")
+    N = params.N if params.topo != KA_CUBIC else params.L ** params.d
+    z = params.z if params.topo != KA_CUBIC else 2 * params.d
+    t = {"nbr": np.zeros(N * z, np.int32), "class_off": np.zeros(nb.value + 1, np.int64),
+         "bu": np.zeros(nb.value, np.int32), "bv": np.zeros(nb.value, np.int32),
+         "bid": np.zeros(nb.value, np.int64)}
+    _check(lib.ka_build_topology(C.byref(params), C.byref(nc), C.byref(nb), _ptr(t["nbr"]),
+                           _ptr(t["class_off"]), _ptr(t["bu"]), _ptr(t["bv"]), _ptr(t["bid"])),
+           "ka_build_topology")
+    t["class_off"] = t["class_off"][: nc.value + 1].copy()
+    return t
+
+
+def ka_profile_enable(ctx: Ctx, enable: bool) -> None:
+    _check(load().ka_profile_enable(ctx.handle, 1 if enable else 0), "ka_profile_enable", ctx)
+
+
+def ka_profile_read(ctx: Ctx):
+    ms, n = C.c_double(0), C.c_int64(0)
+    _check(load().ka_profile_read(ctx.handle, C.byref(ms), C.byref(n)), "ka_profile_read", ctx)
+    return ms.value, n.value
+
+
+def ka_destroy(ctx: Ctx) -> None:
+    if ctx and ctx.handle.value:
+        st = load().ka_destroy(ctx.handle)
+        ctx.handle = C.c_void_p(0)
+        _check(st, "ka_destroy")
+
+
+def ka_last_error(ctx: Ctx) -> str:
+    return load().ka_last_error(ctx.handle).decode()
+
+
+class Simulation:
+    """One context whose device buffer is a torch tensor on torch's current stream.
+
+    >>> sim = Simulation(topo=KA_CUBIC, d=3, L=16, m=3, replicas=64)
+    >>> sim.init(seed=1, rho=0.7); sim.sweep(10); sweep, counts = sim.observe()
+    """
+
+    def __init__(self, device: int = 0, stream=None, **kw):
+        import torch
+
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        params, keep = make_params(stream=stream.cuda_stream, device=device, **kw)
+        nbytes = ka_required_bytes(params)
+        self.buffer = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{device}")
+        self.ctx = ka_create_in(params, self.buffer.data_ptr(), nbytes, keep=(keep, self.buffer))
+        self.info = ka_info(self.ctx)
+
+    def init(self, seed: int, rho: float) -> None:
+        ka_init(self.ctx, seed, rho)
+
+    def sweep(self, n: int) -> None:
+        ka_sweep(self.ctx, n)
+
+    def observe(self):
+        return ka_observe(self.ctx)
+
+    def get_state(self):
+        return ka_get_state(self.ctx)
+
+    def set_state(self, n, n0, p, sweep: int, seed: int) -> None:
+        ka_set_state(self.ctx, n, n0, p, sweep, seed)
+
+    def close(self) -> None:
+        ka_destroy(self.ctx)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self.ctx:
+                ka_destroy(self.ctx)
+        except Exception:
+            pass
+
+
+def correlation(counts: np.ndarray, N: int, K: int) -> float:
+    """C(t) of section 3.3 averaged over replicas, rho = K / N."""
+    rho = K / N
+    return float(((counts[:, 1] - N * rho * rho) / (N * rho * (1.0 - rho))).mean())
+
+
+def persistence(counts: np.ndarray, K: int) -> float:
+    """Fraction of the initial particles whose site has never changed."""
+    return float((counts[:, 2] / K).mean())

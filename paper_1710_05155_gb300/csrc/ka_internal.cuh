@@ -1,0 +1,138 @@
+// ka_internal.cuh -- internal declarations of the GB300 multispin KA library.
+//
+// Device layout of one state plane set (n, n0, p): P = W / V planes, each
+// [N][V] uint64 with V = 2 words per site when the word count W = R / 64 is
+// even, else V = 1.  Word w of site i lives in plane w / V at element
+// i * V + w % V.  With V = 2 one 16-byte load brings both words of a Philox
+// block (words 2q and 2q+1 share the counter (t, c, b, q)).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ka.h"
+
+#define KA_HD __host__ __device__ __forceinline__
+
+namespace ka {
+
+constexpr uint32_t kTagInit = 0xFFFFFFFFu;   // counter word c1 of the initial-state keys
+constexpr uint32_t kTagGraph = 0xFFFFFFFEu;  // counter word c1 of the graph shuffle
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+// Round keys of Philox4x32-10 for one seed: rk[2r], rk[2r+1] is the key of
+// round r (the key is bumped by the Weyl constants between rounds).
+struct RoundKeys {
+  uint32_t k[20];
+};
+
+inline RoundKeys round_keys(uint64_t seed) {
+  RoundKeys rk;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk.k[2 * r] = k0;
+    rk.k[2 * r + 1] = k1;
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+  return rk;
+}
+
+// Philox4x32-10 block (Salmon et al., SC'11) with precomputed round keys.
+KA_HD uint4 philox(uint4 c, const RoundKeys& rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+#ifdef __CUDA_ARCH__
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+#else
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * c.x, p1 = (uint64_t)kPhiloxM1 * c.z;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#endif
+    c = make_uint4(hi1 ^ c.y ^ rk.k[2 * r], lo1, hi0 ^ c.w ^ rk.k[2 * r + 1], lo0);
+  }
+  return c;
+}
+
+KA_HD uint64_t lo64(uint4 b) { return (uint64_t)b.x | ((uint64_t)b.y << 32); }
+KA_HD uint64_t hi64(uint4 b) { return (uint64_t)b.z | ((uint64_t)b.w << 32); }
+
+// --------------------------------------------------------------------------
+// Host-side topology (built at create, uploaded once)
+// --------------------------------------------------------------------------
+struct Topology {
+  int64_t N = 0;
+  int z = 0;
+  std::vector<int32_t> nbr;        // [N][z]
+  std::vector<int64_t> class_off;  // [nclass + 1]
+  std::vector<int32_t> bu, bv;     // bonds grouped by class
+  std::vector<int64_t> bid;        // Philox bond id
+  int attempts = 0;
+  int64_t nclass() const { return (int64_t)class_off.size() - 1; }
+};
+
+// Returns "" on success, else an error message.
+std::string build_cubic_tables(int d, int L, Topology& t);
+std::string build_rrg(int64_t N, int z, uint64_t graph_seed, Topology& t);
+std::string build_graph(int64_t N, int z, const int32_t* nbr, Topology& t);
+
+// --------------------------------------------------------------------------
+// Kernel launchers
+// --------------------------------------------------------------------------
+struct Planes {
+  uint64_t* n;
+  uint64_t* n0;
+  uint64_t* p;
+  int64_t N;
+  int W;  // words per site (R / 64)
+  int V;  // words per site per plane (1 or 2)
+  int P;  // planes (W / V)
+  KA_HD size_t plane_elems() const { return (size_t)N * V; }
+};
+
+struct CubicShape {
+  int d, L, m;
+};
+
+// One group (mu, par) of four classes on plane q, sweep index t.
+cudaError_t launch_cubic_group(const Planes& pl, int q, const CubicShape& s, int mu, int par,
+                               uint32_t t, const RoundKeys& rk, cudaStream_t st);
+
+struct GraphDev {
+  const int32_t* nbr;  // [N][z]
+  const int32_t* bu;
+  const int32_t* bv;
+  const uint32_t* bid;
+  int z, m;
+};
+// Class c (bonds [off, off + count) of the class-ordered bond arrays), all planes.
+cudaError_t launch_graph_class(const Planes& pl, const GraphDev& g, int64_t off, int64_t count,
+                               uint32_t cls, uint32_t t, const RoundKeys& rk, cudaStream_t st);
+
+struct InitScratch {
+  uint32_t* hist;      // [R][256]
+  uint64_t* pre_key;   // [R] decided high bits of the threshold key
+  uint32_t* pre_idx;   // [R] decided high bits of the threshold site
+  int64_t* krem;       // [R] rank still to place inside the current bucket
+  int32_t* unresolved; // [1] any replica whose threshold key is tied
+};
+cudaError_t launch_init(const Planes& pl, const InitScratch& s, int R, int64_t K,
+                        const RoundKeys& rk, cudaStream_t st);
+
+// canonical [W][N] <-> device [P][N][2] (V = 2 only)
+cudaError_t launch_to_device(const uint64_t* canonical, uint64_t* device_layout, int64_t N, int P,
+                             cudaStream_t st);
+cudaError_t launch_to_canonical(const uint64_t* device_layout, uint64_t* canonical, int64_t N,
+                                int P, cudaStream_t st);
+
+cudaError_t launch_observe(const Planes& pl, int R, unsigned long long* counts_dev,
+                           cudaStream_t st);
+
+}  // namespace ka

@@ -1,0 +1,126 @@
+// ka_observe.cu -- per-replica observables by vertical popcounts.
+//
+// Section 3.3 computes overlaps as bitwise ANDs of multispin words and
+// counts their ones.  Here the counts are needed per replica, i.e. per bit
+// position, summed over sites: for every replica r
+//   particles   = sum_i n_i
+//   overlap     = sum_i n_i & n0_i        (the q_i(t) = n_i(t) n_i(0) of section 2.2)
+//   persist_occ = sum_i n0_i & p_i
+//   persist_all = sum_i p_i
+//
+// Each thread adds up to 255 words into bit-sliced counters (8 slices: one
+// uint64 per binary digit, so all 64 replicas count in parallel with a
+// ripple adder).  Lanes holding the same word position are then summed in
+// bit-sliced form through warp shuffles, the warp total is turned into one
+// integer per replica, and blocks accumulate in shared memory before one
+// 64-bit atomic per counter goes to global memory.
+#include "ka_internal.cuh"
+
+namespace ka {
+namespace {
+
+constexpr int kSlices = 8;        // per-thread counters hold up to 255
+constexpr int kPerThread = 255;   // words per thread
+constexpr int kWide = kSlices + 5;  // after summing 32 lanes
+
+__device__ __forceinline__ void ripple_add(uint64_t (&c)[kSlices], uint64_t x) {
+#pragma unroll
+  for (int s = 0; s < kSlices; ++s) {
+    const uint64_t k = c[s] & x;
+    c[s] ^= x;
+    x = k;
+  }
+}
+
+// add the counter of lane (lane ^ off) into this lane's, bit-sliced
+__device__ __forceinline__ void shfl_add(uint64_t (&c)[kWide], int off) {
+  uint64_t carry = 0;
+#pragma unroll
+  for (int s = 0; s < kWide; ++s) {
+    const uint64_t o = __shfl_xor_sync(0xffffffffu, c[s], off);
+    const uint64_t sum = c[s] ^ o ^ carry;
+    carry = (c[s] & o) | (carry & (c[s] | o));
+    c[s] = sum;
+  }
+}
+
+template <int V>
+__global__ void __launch_bounds__(256) k_observe(Planes pl, unsigned long long* counts) {
+  __shared__ unsigned int acc[4][64 * V];
+  const int q = blockIdx.y;
+  for (int k = threadIdx.x; k < 4 * 64 * V; k += blockDim.x) (&acc[0][0])[k] = 0;
+  __syncthreads();
+
+  const size_t E = pl.plane_elems();
+  const size_t base = (size_t)q * E;
+  // element e of the plane holds word h = e % V of site e / V; blockDim and
+  // the stride are even, so a thread always sees the same h
+  const size_t e0 = (size_t)blockIdx.x * blockDim.x * kPerThread + threadIdx.x;
+  uint64_t c[4][kSlices];
+#pragma unroll
+  for (int o = 0; o < 4; ++o)
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) c[o][s] = 0;
+  for (int k = 0; k < kPerThread; ++k) {
+    const size_t e = e0 + (size_t)k * blockDim.x;
+    if (e >= E) break;
+    const uint64_t n = pl.n[base + e], n0 = pl.n0[base + e], p = pl.p[base + e];
+    ripple_add(c[0], n);
+    ripple_add(c[1], n & n0);
+    ripple_add(c[2], n0 & p);
+    ripple_add(c[3], p);
+  }
+
+  const int lane = threadIdx.x & 31;
+  const int h = lane % V;
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    uint64_t w[kWide];
+#pragma unroll
+    for (int s = 0; s < kWide; ++s) w[s] = (s < kSlices) ? c[o][s] : 0;
+    // sum lanes with the same word position (stride V)
+#pragma unroll
+    for (int off = 16; off >= V; off >>= 1) shfl_add(w, off);
+    // lanes 0 .. V-1 hold the totals of word positions 0 .. V-1; every lane
+    // extracts replicas (bit positions) lane and lane + 32 of each
+#pragma unroll
+    for (int hh = 0; hh < V; ++hh) {
+      unsigned int lo = 0, hi = 0;
+#pragma unroll
+      for (int s = 0; s < kWide; ++s) {
+        const uint64_t t = __shfl_sync(0xffffffffu, w[s], hh);
+        lo |= (unsigned int)((t >> lane) & 1u) << s;
+        hi |= (unsigned int)((t >> (lane + 32)) & 1u) << s;
+      }
+      if (lo) atomicAdd(&acc[o][hh * 64 + lane], lo);
+      if (hi) atomicAdd(&acc[o][hh * 64 + lane + 32], hi);
+    }
+  }
+  (void)h;
+  __syncthreads();
+  for (int k = threadIdx.x; k < 4 * 64 * V; k += blockDim.x) {
+    const int o = k / (64 * V), rb = k % (64 * V);  // rb = h * 64 + bit
+    const unsigned int v = acc[o][rb];
+    if (v) {
+      const int r = (q * V + rb / 64) * 64 + (rb % 64);
+      atomicAdd(&counts[(size_t)r * 4 + o], (unsigned long long)v);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_observe(const Planes& pl, int R, unsigned long long* counts_dev,
+                           cudaStream_t st) {
+  cudaError_t err = cudaMemsetAsync(counts_dev, 0, (size_t)R * 4 * sizeof(unsigned long long), st);
+  if (err != cudaSuccess) return err;
+  const size_t per_block = (size_t)256 * kPerThread;
+  dim3 grid((unsigned)((pl.plane_elems() + per_block - 1) / per_block), (unsigned)pl.P);
+  if (pl.V == 2)
+    k_observe<2><<<grid, 256, 0, st>>>(pl, counts_dev);
+  else
+    k_observe<1><<<grid, 256, 0, st>>>(pl, counts_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace ka
