@@ -56,6 +56,8 @@ def _load():
         lib.ora_philox4x32_10.restype = None
         lib.ora_gate_word.argtypes = [U64, I64, I64, I64, I64]
         lib.ora_gate_word.restype = U64
+        lib.ora_cubic_gate_word.argtypes = [U64, I64, I64, I64, I64, I]
+        lib.ora_cubic_gate_word.restype = U64
         lib.ora_particles.argtypes = [C.c_double, I64]
         lib.ora_particles.restype = I64
         lib.ora_cubic_tables.argtypes = [I, I, i32p, i64p, i32p, i32p, i64p, C.POINTER(I64)]
@@ -66,9 +68,9 @@ def _load():
         lib.ora_local_move.argtypes = [I, I, I, I, u8p, u8p, I, C.POINTER(I), C.POINTER(I)]
         lib.ora_init.argtypes = [I64, I64, I64, U64, I64, u8p, u8p, u8p]
         lib.ora_class_step.argtypes = [I64, I, i32p, I, I64, i32p, i32p, i64p, I64, I64, U64,
-                                       I64, I64, u8p, u8p]
+                                       I64, I64, I, u8p, u8p]
         lib.ora_sweeps.argtypes = [I64, I, i32p, I, I64, i64p, i32p, i32p, i64p, U64, I64, I64,
-                                   I64, I64, u8p, u8p]
+                                   I, I64, I64, u8p, u8p]
         lib.ora_observe.argtypes = [I64, I64, u8p, u8p, u8p, i64p]
         lib.ora_observe.restype = None
         for name in ("ora_cubic_tables", "ora_rrg_build", "ora_graph_edges", "ora_graph_classes",
@@ -92,7 +94,13 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 
 def gate_word(seed: int, t: int, cls: int, bond: int, w: int) -> int:
+    """Gate word on a graph (edge id `bond`)."""
     return int(_load().ora_gate_word(seed, t, cls, bond, w))
+
+
+def cubic_gate_word(seed: int, t: int, cls: int, bond: int, w: int, L: int) -> int:
+    """Gate word on a periodic cubic lattice of side L (base site `bond`)."""
+    return int(_load().ora_cubic_gate_word(seed, t, cls, bond, w, L))
 
 
 def particles(rho: float, N: int) -> int:
@@ -102,8 +110,9 @@ def particles(rho: float, N: int) -> int:
 class Topology:
     """Neighbour table and bond classes of one lattice or graph."""
 
-    def __init__(self, N, z, nbr, class_off, bu, bv, bid):
+    def __init__(self, N, z, nbr, class_off, bu, bv, bid, cubic_L=0):
         self.N, self.z = int(N), int(z)
+        self.cubic_L = int(cubic_L)  # side of a cubic lattice (its gate stream), 0 for graphs
         self.nbr = nbr
         self.class_off, self.bu, self.bv, self.bid = class_off, bu, bv, bid
 
@@ -128,7 +137,7 @@ def cubic(d: int, L: int) -> Topology:
     bid = np.zeros(d * N, np.int64)
     out = C.c_int64(0)
     _check(lib.ora_cubic_tables(d, L, nbr, off, bu, bv, bid, C.byref(out)), "cubic_tables")
-    return Topology(N, z, nbr, off, bu, bv, bid)
+    return Topology(N, z, nbr, off, bu, bv, bid, cubic_L=L)
 
 
 def rrg_neighbours(N: int, z: int, graph_seed: int, max_attempts: int = 1 << 20):
@@ -202,14 +211,15 @@ def class_step(topo: Topology, m: int, st: State, cls: int, seed: int, t: int | 
                                   np.ascontiguousarray(topo.bu[c0:c1]),
                                   np.ascontiguousarray(topo.bv[c0:c1]),
                                   np.ascontiguousarray(topo.bid[c0:c1]),
-                                  cls, st.t if t is None else t, seed, st.r0, st.Rs, st.n, st.p),
+                                  cls, st.t if t is None else t, seed, st.r0, st.Rs, topo.cubic_L,
+                                  st.n, st.p),
            "class_step")
 
 
 def sweeps(topo: Topology, m: int, st: State, seed: int, nsweeps: int) -> State:
     _check(_load().ora_sweeps(topo.N, topo.z, topo.nbr, m, topo.nclass, topo.class_off,
-                              topo.bu, topo.bv, topo.bid, seed, st.r0, st.Rs, st.t, nsweeps,
-                              st.n, st.p), "sweeps")
+                              topo.bu, topo.bv, topo.bid, seed, st.r0, st.Rs, topo.cubic_L, st.t,
+                              nsweeps, st.n, st.p), "sweeps")
     st.t += nsweeps
     return st
 

@@ -85,9 +85,30 @@ static void ora_philox_seeded(uint64_t seed, uint32_t a, uint32_t b, uint32_t c,
 
 uint64_t ora_gate_word(uint64_t seed, int64_t t, int64_t cls, int64_t bond, int64_t w)
 {
+    /* graphs: one block per (sweep, class, edge, word pair), half w mod 2 */
     uint32_t o[4];
     ora_philox_seeded(seed, (uint32_t)t, (uint32_t)cls, (uint32_t)bond, (uint32_t)(w / 2), o);
     if (w % 2 == 0)
+        return (uint64_t)o[0] | ((uint64_t)o[1] << 32);
+    return (uint64_t)o[2] | ((uint64_t)o[3] << 32);
+}
+
+uint64_t ora_cubic_gate_word(uint64_t seed, int64_t t, int64_t cls, int64_t bond, int64_t w,
+                             int L)
+{
+    /* cubic lattices: the bonds of classes 4g + 2b and 4g + 2b + 1 that start
+     * at pencil positions 4k + 2b and 4k + 2b + 1 share one block, counter
+     * (sweep, 4g + 2b, base site of the first of the two, word); the first
+     * bond takes half 0, the second half 1 */
+    int64_t mu = cls / 8, a = cls % 4;
+    int64_t stride = 1;
+    for (int64_t k = 0; k < mu; k++)
+        stride *= L;
+    int64_t first = bond - (a % 2) * stride;
+    uint32_t o[4];
+    ora_philox_seeded(seed, (uint32_t)t, (uint32_t)(cls - (cls % 2)), (uint32_t)first,
+                      (uint32_t)w, o);
+    if (a % 2 == 0)
         return (uint64_t)o[0] | ((uint64_t)o[1] << 32);
     return (uint64_t)o[2] | ((uint64_t)o[3] << 32);
 }
@@ -536,7 +557,7 @@ int ora_init(int64_t N, int64_t r0, int64_t Rs, uint64_t seed, int64_t K, uint8_
 
 int ora_class_step(int64_t N, int z, const int32_t *nbr, int m, int64_t nb, const int32_t *bu,
                    const int32_t *bv, const int64_t *bid, int64_t cls, int64_t t, uint64_t seed,
-                   int64_t r0, int64_t Rs, uint8_t *n, uint8_t *p)
+                   int64_t r0, int64_t Rs, int cubic_L, uint8_t *n, uint8_t *p)
 {
     if (Rs <= 0)
         return ORA_OK;
@@ -549,7 +570,8 @@ int ora_class_step(int64_t N, int z, const int32_t *nbr, int m, int64_t nb, cons
     for (int64_t b = 0; b < nb; b++) {
         int64_t i = bu[b], j = bv[b];
         for (int64_t w = w_first; w <= w_last; w++)
-            gate[w - w_first] = ora_gate_word(seed, t, cls, bid[b], w);
+            gate[w - w_first] = cubic_L > 0 ? ora_cubic_gate_word(seed, t, cls, bid[b], w, cubic_L)
+                                            : ora_gate_word(seed, t, cls, bid[b], w);
         for (int64_t rr = 0; rr < Rs; rr++) {
             int64_t r = r0 + rr;
             int g = (int)((gate[r / 64 - w_first] >> (r % 64)) & 1u);
@@ -579,14 +601,14 @@ int ora_class_step(int64_t N, int z, const int32_t *nbr, int m, int64_t nb, cons
 
 int ora_sweeps(int64_t N, int z, const int32_t *nbr, int m, int64_t nclass,
                const int64_t *class_off, const int32_t *bu, const int32_t *bv, const int64_t *bid,
-               uint64_t seed, int64_t r0, int64_t Rs, int64_t t0, int64_t nsweeps, uint8_t *n,
-               uint8_t *p)
+               uint64_t seed, int64_t r0, int64_t Rs, int cubic_L, int64_t t0, int64_t nsweeps,
+               uint8_t *n, uint8_t *p)
 {
     for (int64_t s = 0; s < nsweeps; s++) {
         for (int64_t c = 0; c < nclass; c++) {
             int64_t off = class_off[c];
             int rc = ora_class_step(N, z, nbr, m, class_off[c + 1] - off, bu + off, bv + off,
-                                    bid + off, c, t0 + s, seed, r0, Rs, n, p);
+                                    bid + off, c, t0 + s, seed, r0, Rs, cubic_L, n, p);
             if (rc != ORA_OK)
                 return rc;
         }

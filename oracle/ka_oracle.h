@@ -23,8 +23,16 @@ extern "C" {
 /* Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11). */
 void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
-/* 64-bit random gate word for word w of bond `bond` in class `cls` at sweep t. */
+/* 64-bit random gate word for word w of edge `bond` in class `cls` at sweep t
+ * on a graph: half (w mod 2) of the block at counter (t, cls, bond, w / 2). */
 uint64_t ora_gate_word(uint64_t seed, int64_t t, int64_t cls, int64_t bond, int64_t w);
+
+/* The same on a periodic cubic lattice of side L, where `bond` is the base
+ * site: bonds starting at pencil positions 4k + 2b and 4k + 2b + 1 (classes
+ * 4g + 2b and 4g + 2b + 1) share the block at counter
+ * (t, 4g + 2b, base site of the first, w), the first taking half 0. */
+uint64_t ora_cubic_gate_word(uint64_t seed, int64_t t, int64_t cls, int64_t bond, int64_t w,
+                             int L);
 
 /* K = rho*N rounded half away from zero. */
 int64_t ora_particles(double rho, int64_t N);
@@ -64,16 +72,17 @@ int ora_local_move(int z, int m, int ni, int nj, const uint8_t *others_i,
 int ora_init(int64_t N, int64_t r0, int64_t Rs, uint64_t seed, int64_t K,
              uint8_t *n, uint8_t *n0, uint8_t *p);
 
-/* One class of bonds at sweep t. */
+/* One class of bonds at sweep t.  cubic_L > 0 selects the cubic-lattice gate
+ * stream (ora_cubic_gate_word with side cubic_L), 0 the graph stream. */
 int ora_class_step(int64_t N, int z, const int32_t *nbr, int m, int64_t nb,
                    const int32_t *bu, const int32_t *bv, const int64_t *bid,
                    int64_t cls, int64_t t, uint64_t seed, int64_t r0, int64_t Rs,
-                   uint8_t *n, uint8_t *p);
+                   int cubic_L, uint8_t *n, uint8_t *p);
 
 /* nsweeps sweeps starting at sweep index t0 (all classes in order). */
 int ora_sweeps(int64_t N, int z, const int32_t *nbr, int m, int64_t nclass,
                const int64_t *class_off, const int32_t *bu, const int32_t *bv,
-               const int64_t *bid, uint64_t seed, int64_t r0, int64_t Rs,
+               const int64_t *bid, uint64_t seed, int64_t r0, int64_t Rs, int cubic_L,
                int64_t t0, int64_t nsweeps, uint8_t *n, uint8_t *p);
 
 /* Per replica: particles, overlap (n and n0), persist_occ (n0 and p),

@@ -88,7 +88,8 @@ def test_order_inside_a_class_does_not_matter():
         lo, hi = topo.class_off[c], topo.class_off[c + 1]
         p = lo + rng.permutation(hi - lo)
         perm_bu[lo:hi], perm_bv[lo:hi], perm_bid[lo:hi] = topo.bu[p], topo.bv[p], topo.bid[p]
-    shuffled = O.Topology(topo.N, topo.z, topo.nbr, topo.class_off, perm_bu, perm_bv, perm_bid)
+    shuffled = O.Topology(topo.N, topo.z, topo.nbr, topo.class_off, perm_bu, perm_bv, perm_bid,
+                          cubic_L=topo.cubic_L)
     a = O.init(topo.N, 64, 9, 0.7)
     b = a.copy()
     O.sweeps(topo, 3, a, 9, 6)
@@ -105,6 +106,26 @@ def test_replica_independent_of_its_word():
         O.sweeps(topo, 2, one, 21, 15)
         assert (one.n[:, 0] == full.n[:, r]).all()
         assert (one.p[:, 0] == full.p[:, r]).all()
+
+
+def test_graph_gate_bit_convention():
+    # on a graph the gate of word w of edge e is half (w mod 2) of block (t, c, e, w // 2)
+    topo = O.rrg(64, 4, 3)
+    R, seed, t = 192, 5, 2
+    for c in range(topo.nclass):
+        lo, hi = topo.class_off[c], topo.class_off[c + 1]
+        b = lo
+        u = int(topo.bu[b])
+        st = O.State(topo.N, R)
+        st.n[u, :] = 1
+        st.n0[:] = st.n
+        st.p[:] = 1
+        O.class_step(topo, 0, st, c, seed, t=t)
+        for r in range(R):
+            g = (O.gate_word(seed, t, c, int(topo.bid[b]), r // 64) >> (r % 64)) & 1
+            # the lone particle sits on one end of this edge; other edges of the
+            # class do not touch it (strong matching)
+            assert st.n[u, r] == 1 - g
 
 
 def test_sweeps_compose():
@@ -267,6 +288,7 @@ def test_gate_bit_convention_in_class_step():
     # a lone particle has no constraint, so on a bond touching it it hops iff
     # the replica's gate bit is set: replica r reads bit r % 64 of gate word r // 64
     topo = O.cubic(2, 8)
+    assert topo.cubic_L == 8
     R, seed, t = 192, 77, 5
     for c in range(topo.nclass):
         lo, hi = topo.class_off[c], topo.class_off[c + 1]
@@ -279,5 +301,5 @@ def test_gate_bit_convention_in_class_step():
             st.p[:] = 1
             O.class_step(topo, 0, st, c, seed, t=t)
             for r in range(R):
-                g = (O.gate_word(seed, t, c, int(topo.bid[b]), r // 64) >> (r % 64)) & 1
+                g = (O.cubic_gate_word(seed, t, c, int(topo.bid[b]), r // 64, 8) >> (r % 64)) & 1
                 assert st.n[9, r] == 1 - g

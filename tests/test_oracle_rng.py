@@ -45,9 +45,27 @@ def test_gate_word_layout():
             assert O.gate_word(seed, t, c, b, w) == int(lo) | (int(hi) << 32)
 
 
+def test_cubic_gate_word_layout():
+    # bonds at pencil positions 4k + 2b and 4k + 2b + 1 share the block with
+    # counter (t, 4g + 2b, first base site, w): half 0 for the first, 1 for the second
+    seed, L = 77, 8
+    for mu, stride in ((0, 1), (1, 8), (2, 64)):
+        for par in (0, 1):
+            for a in range(4):
+                cls = 4 * (2 * mu + par) + a
+                for base in (3 * stride * 4 + 5 if mu else 36, 100):
+                    for w in range(3):
+                        first = base - (a % 2) * stride
+                        blk = O.philox4x32_10([9, cls - cls % 2, first, w], [seed, 0])
+                        lo, hi = (blk[0], blk[1]) if a % 2 == 0 else (blk[2], blk[3])
+                        got = O.cubic_gate_word(seed, 9, cls, base, w, L)
+                        assert got == int(lo) | (int(hi) << 32)
+
+
 def test_gate_bits_are_fair():
     # Bernoulli(1/2) per replica: 64 * 4000 bits, mean within 5 sigma of 1/2
-    words = [O.gate_word(1, t, 5, b, 0) for t in range(40) for b in range(100)]
+    words = [O.gate_word(1, t, 5, b, 0) for t in range(40) for b in range(50)]
+    words += [O.cubic_gate_word(1, t, 5, b, 1, 16) for t in range(40) for b in range(50)]
     ones = sum(bin(w).count("1") for w in words)
     n = 64 * len(words)
     assert abs(ones - n / 2) < 5 * math.sqrt(n / 4)
