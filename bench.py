@@ -169,7 +169,8 @@ def run_native(args, rank: int, world: int) -> None:
         sim.init(SEED + 1000 * rank, rho)
         sims.append(sim)
     counts_dev = [torch.zeros((R, 4), dtype=torch.int64, device=f"cuda:{dev}") for _ in sims]
-    P = sims[0].info["words"] // 2 if sims[0].info["words"] % 2 == 0 else sims[0].info["words"]
+    P = sims[0].info["planes"]
+    V = sims[0].info["plane_words"]
     groups = 2 * D
     launches_per_step = len(sims) * (P * S * groups + 1)
 
@@ -209,7 +210,6 @@ def run_native(args, rank: int, world: int) -> None:
     kms, nl = K.ka_profile_read(sims[0].ctx)
     K.ka_profile_enable(sims[0].ctx, False)
     avg_launch_ms = kms / max(nl, 1)
-    V = 2 if WORDS % 2 == 0 else 1
     bytes_per_launch = BYTES_PER_SITE_WORD_SWEEP * N_SITES * V / groups
     achieved = bytes_per_launch / (avg_launch_ms / 1000.0) / 1e9
     peak, peak_kind = _peaks()

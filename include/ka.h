@@ -117,6 +117,8 @@ typedef struct {
     int32_t kernel;     /* 0 = cubic pencil kernel, 1 = edge-gather kernel */
     int32_t rrg_attempts; /* configuration-model attempts (KA_RRG) */
     size_t device_bytes;  /* device memory the context uses */
+    int32_t planes;       /* device state planes per array (sweep launches per class group) */
+    int32_t plane_words;  /* words per site in one plane */
 } ka_info_t;
 
 /* Device bytes ka_create_in needs for these parameters. */

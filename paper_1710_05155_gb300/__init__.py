@@ -40,7 +40,8 @@ class ka_info_t(C.Structure):
     _fields_ = [("N", C.c_int64), ("z", C.c_int32), ("m", C.c_int32), ("replicas", C.c_int32),
                 ("words", C.c_int32), ("nclass", C.c_int64), ("nbonds", C.c_int64),
                 ("sweep", C.c_int64), ("K", C.c_int64), ("seed", C.c_uint64),
-                ("kernel", C.c_int32), ("rrg_attempts", C.c_int32), ("device_bytes", C.c_size_t)]
+                ("kernel", C.c_int32), ("rrg_attempts", C.c_int32), ("device_bytes", C.c_size_t),
+                ("planes", C.c_int32), ("plane_words", C.c_int32)]
 
 
 _lib = None

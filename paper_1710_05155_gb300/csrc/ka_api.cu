@@ -63,8 +63,7 @@ const char* check_params(const ka_params* p, Shape& s) {
   s.R = p->replicas;
   if (s.R <= 0 || s.R % 64 || s.R > 65536) return "replicas must be a positive multiple of 64, at most 65536";
   s.W = s.R / 64;
-  s.V = (s.W % 2 == 0) ? 2 : 1;
-  s.P = s.W / s.V;
+  s.V = (s.W % 2 == 0) ? 2 : 1;  // refined below for the cubic pencil kernel
   if (p->topo == KA_CUBIC) {
     s.d = p->d;
     s.L = p->L;
@@ -94,6 +93,10 @@ const char* check_params(const ka_params* p, Shape& s) {
     return "unknown topology";
   }
   if (s.m < 0 || s.m > s.z - 1) return "m must be in [0, z-1]";
+  // words per site and plane: the pencil kernel reads a whole 32-byte sector
+  // per site when 4 words fit; the edge-gather kernel pairs at most 2
+  if (s.pencil && s.W % 4 == 0) s.V = 4;
+  s.P = s.W / s.V;
   return nullptr;
 }
 
@@ -109,7 +112,7 @@ Layout layout_of(const Shape& s) {
   l.n = take(plane);
   l.n0 = take(plane);
   l.p = take(plane);
-  l.stage = (s.V == 2) ? take(plane) : 0;  // layout conversion of get/set_state
+  l.stage = (s.V > 1) ? take(plane) : 0;  // layout conversion of get/set_state
   l.counts = take((size_t)s.R * 4 * sizeof(unsigned long long));
   l.hist = take((size_t)s.R * 256 * sizeof(uint32_t));
   l.pre_key = take((size_t)s.R * sizeof(uint64_t));
@@ -175,7 +178,7 @@ ka_status create_common(const ka_params* params, void* buf, size_t bytes, bool o
   c->pl.V = s.V;
   c->pl.P = s.P;
   c->counts_dev = (unsigned long long*)(base + l.counts);
-  c->stage = (s.V == 2) ? (uint64_t*)(base + l.stage) : nullptr;
+  c->stage = (s.V > 1) ? (uint64_t*)(base + l.stage) : nullptr;
   c->is.hist = (uint32_t*)(base + l.hist);
   c->is.pre_key = (uint64_t*)(base + l.pre_key);
   c->is.pre_idx = (uint32_t*)(base + l.pre_idx);
@@ -206,6 +209,7 @@ ka_status create_common(const ka_params* params, void* buf, size_t bytes, bool o
     c->g.bid = (const uint32_t*)(base + l.bid);
     c->g.z = s.z;
     c->g.m = s.m;
+    c->g.cubic_L = (s.topo == KA_CUBIC) ? s.L : 0;
     std::vector<uint32_t> bid32(c->host.bid.begin(), c->host.bid.end());
     cudaError_t e = cudaMemcpyAsync((void*)c->g.nbr, c->host.nbr.data(),
                                     c->host.nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
@@ -394,8 +398,8 @@ ka_status ka_get_state(ka_ctx* c, uint64_t* n, uint64_t* n0, uint64_t* p) {
   for (int k = 0; k < 3 && !e; ++k) {
     if (!dst[k]) continue;
     const uint64_t* from = src[k];
-    if (c->pl.V == 2) {
-      e = ka::launch_to_canonical(src[k], c->stage, c->N, c->pl.P, c->stream);
+    if (c->pl.V > 1) {
+      e = ka::launch_to_canonical(src[k], c->stage, c->N, c->pl.P, c->pl.V, c->stream);
       from = c->stage;
     }
     // stream order keeps the next conversion from overwriting the staging
@@ -416,9 +420,9 @@ ka_status ka_set_state(ka_ctx* c, const uint64_t* n, const uint64_t* n0, const u
   uint64_t* dst[3] = {c->pl.n, c->pl.n0, c->pl.p};
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < 3 && !e; ++k) {
-    if (c->pl.V == 2) {
+    if (c->pl.V > 1) {
       e = cudaMemcpyAsync(c->stage, src[k], bytes, cudaMemcpyHostToDevice, c->stream);
-      if (!e) e = ka::launch_to_device(c->stage, dst[k], c->N, c->pl.P, c->stream);
+      if (!e) e = ka::launch_to_device(c->stage, dst[k], c->N, c->pl.P, c->pl.V, c->stream);
     } else {
       e = cudaMemcpyAsync(dst[k], src[k], bytes, cudaMemcpyHostToDevice, c->stream);
     }
@@ -456,6 +460,8 @@ ka_status ka_info(const ka_ctx* c, ka_info_t* out) {
   out->kernel = c->pencil ? 0 : 1;
   out->rrg_attempts = c->host.attempts;
   out->device_bytes = c->bytes;
+  out->planes = c->pl.P;
+  out->plane_words = c->pl.V;
   return KA_OK;
 }
 

@@ -218,7 +218,9 @@ cudaError_t launch_init(const Planes& pl, const InitScratch& s, int R, int64_t K
     if ((err = cudaGetLastError())) return err;
   }
   dim3 mgrid((unsigned)((pl.N * pl.V + 255) / 256), (unsigned)pl.P);
-  if (pl.V == 2)
+  if (pl.V == 4)
+    k_init_mark<4><<<mgrid, 256, 0, st>>>(a, pl);
+  else if (pl.V == 2)
     k_init_mark<2><<<mgrid, 256, 0, st>>>(a, pl);
   else
     k_init_mark<1><<<mgrid, 256, 0, st>>>(a, pl);

@@ -1,10 +1,10 @@
 // ka_internal.cuh -- internal declarations of the GB300 multispin KA library.
 //
 // Device layout of one state plane set (n, n0, p): P = W / V planes, each
-// [N][V] uint64 with V = 2 words per site when the word count W = R / 64 is
-// even, else V = 1.  Word w of site i lives in plane w / V at element
-// i * V + w % V.  With V = 2 one 16-byte load brings both words of a Philox
-// block (words 2q and 2q+1 share the counter (t, c, b, q)).
+// [N][V] uint64, W = R / 64 words per site.  Word w of site i lives in plane
+// w / V at element i * V + w % V.  Cubic lattices on the pencil kernel use
+// V = 4 (one 32-byte sector per site) when 4 divides W; otherwise V = 2 for
+// even W, else 1.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -48,14 +48,10 @@ inline RoundKeys round_keys(uint64_t seed) {
 KA_HD uint4 philox(uint4 c, const RoundKeys& rk) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-#ifdef __CUDA_ARCH__
-    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
-    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
-#else
+    // one 32 x 32 -> 64-bit multiply per product (a single wide IMAD on the GPU)
     const uint64_t p0 = (uint64_t)kPhiloxM0 * c.x, p1 = (uint64_t)kPhiloxM1 * c.z;
     const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
     const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
-#endif
     c = make_uint4(hi1 ^ c.y ^ rk.k[2 * r], lo1, hi0 ^ c.w ^ rk.k[2 * r + 1], lo0);
   }
   return c;
@@ -111,6 +107,7 @@ struct GraphDev {
   const int32_t* bv;
   const uint32_t* bid;
   int z, m;
+  int cubic_L;  // > 0: the bonds are those of a cubic lattice of this side (its gate stream)
 };
 // Class c (bonds [off, off + count) of the class-ordered bond arrays), all planes.
 cudaError_t launch_graph_class(const Planes& pl, const GraphDev& g, int64_t off, int64_t count,
@@ -126,11 +123,11 @@ struct InitScratch {
 cudaError_t launch_init(const Planes& pl, const InitScratch& s, int R, int64_t K,
                         const RoundKeys& rk, cudaStream_t st);
 
-// canonical [W][N] <-> device [P][N][2] (V = 2 only)
+// canonical [W][N] <-> device [P][N][V]
 cudaError_t launch_to_device(const uint64_t* canonical, uint64_t* device_layout, int64_t N, int P,
-                             cudaStream_t st);
+                             int V, cudaStream_t st);
 cudaError_t launch_to_canonical(const uint64_t* device_layout, uint64_t* canonical, int64_t N,
-                                int P, cudaStream_t st);
+                                int P, int V, cudaStream_t st);
 
 cudaError_t launch_observe(const Planes& pl, int R, unsigned long long* counts_dev,
                            cudaStream_t st);

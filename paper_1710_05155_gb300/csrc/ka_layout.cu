@@ -1,45 +1,45 @@
 // ka_layout.cu -- conversion between the canonical state layout of the ABI
-// ([W][N] uint64, word-plane major) and the device layout ([P][N][V]).
-// Only needed when V = 2; with V = 1 both layouts coincide.
+// ([W][N] uint64, word-plane major) and the device layout ([P][N][V], word w
+// of site i in plane w / V at element i * V + w % V).  With V = 1 both
+// layouts coincide.
 #include "ka_internal.cuh"
 
 namespace ka {
 namespace {
 
-// canonical -> device: dst[q][i][h] = src[2q + h][i]
+// canonical -> device, one thread per (plane, site, word)
 __global__ void k_to_device(const uint64_t* __restrict__ src, uint64_t* __restrict__ dst,
-                            int64_t N, int P) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over P * N sites
-  if (e >= (int64_t)P * N) return;
-  const int64_t q = e / N, i = e - q * N;
-  const ulonglong2 v = make_ulonglong2(src[(2 * q) * N + i], src[(2 * q + 1) * N + i]);
-  reinterpret_cast<ulonglong2*>(dst)[q * N + i] = v;
+                            int64_t N, int P, int V) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // device element
+  if (e >= (int64_t)P * N * V) return;
+  const int64_t q = e / (N * V), r = e - q * N * V;
+  const int64_t i = r / V, h = r - i * V;
+  dst[e] = src[(q * V + h) * N + i];
 }
 
 // device -> canonical
 __global__ void k_to_canonical(const uint64_t* __restrict__ src, uint64_t* __restrict__ dst,
-                               int64_t N, int P) {
+                               int64_t N, int P, int V) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)P * N) return;
-  const int64_t q = e / N, i = e - q * N;
-  const ulonglong2 v = reinterpret_cast<const ulonglong2*>(src)[q * N + i];
-  dst[(2 * q) * N + i] = v.x;
-  dst[(2 * q + 1) * N + i] = v.y;
+  if (e >= (int64_t)P * N * V) return;
+  const int64_t q = e / (N * V), r = e - q * N * V;
+  const int64_t i = r / V, h = r - i * V;
+  dst[(q * V + h) * N + i] = src[e];
 }
 
 }  // namespace
 
 cudaError_t launch_to_device(const uint64_t* canonical, uint64_t* device_layout, int64_t N, int P,
-                             cudaStream_t st) {
-  const int64_t n = (int64_t)P * N;
-  k_to_device<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(canonical, device_layout, N, P);
+                             int V, cudaStream_t st) {
+  const int64_t n = (int64_t)P * N * V;
+  k_to_device<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(canonical, device_layout, N, P, V);
   return cudaGetLastError();
 }
 
 cudaError_t launch_to_canonical(const uint64_t* device_layout, uint64_t* canonical, int64_t N,
-                                int P, cudaStream_t st) {
-  const int64_t n = (int64_t)P * N;
-  k_to_canonical<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(device_layout, canonical, N, P);
+                                int P, int V, cudaStream_t st) {
+  const int64_t n = (int64_t)P * N * V;
+  k_to_canonical<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(device_layout, canonical, N, P, V);
   return cudaGetLastError();
 }
 

@@ -116,7 +116,9 @@ cudaError_t launch_observe(const Planes& pl, int R, unsigned long long* counts_d
   if (err != cudaSuccess) return err;
   const size_t per_block = (size_t)256 * kPerThread;
   dim3 grid((unsigned)((pl.plane_elems() + per_block - 1) / per_block), (unsigned)pl.P);
-  if (pl.V == 2)
+  if (pl.V == 4)
+    k_observe<4><<<grid, 256, 0, st>>>(pl, counts_dev);
+  else if (pl.V == 2)
     k_observe<2><<<grid, 256, 0, st>>>(pl, counts_dev);
   else
     k_observe<1><<<grid, 256, 0, st>>>(pl, counts_dev);

@@ -22,6 +22,7 @@ struct ClassArgs {
   int64_t count;
   int z;
   uint32_t t, cls;
+  uint32_t pair_stride;  // cubic lattices: stride of the bond direction, 0 on graphs
   RoundKeys rk;
 };
 
@@ -99,21 +100,35 @@ __global__ void __launch_bounds__(256) k_graph_class(const ClassArgs a) {
       add3(cv2[h], cv1[h], cv0[h], xv[h] & keep_v);
     }
   }
-  uint32_t c3, half;
-  if constexpr (V == 2) {
-    c3 = (uint32_t)q;
-    half = 0;
-  } else {
-    c3 = (uint32_t)(q >> 1);
-    half = (uint32_t)(q & 1);
-  }
-  const uint4 b = philox(make_uint4(a.t, a.cls, id, c3), a.rk);
+  // gate words.  Graphs: block (t, class, edge, word pair), half = word
+  // parity.  Cubic lattices (one-word planes): bonds of classes 4g+2b and
+  // 4g+2b+1 that start at neighbouring pencil positions share the block
+  // (t, 4g+2b, base site of the first, word), half = class parity.
   uint64_t g[V];
-  if constexpr (V == 2) {
-    g[0] = lo64(b);
-    g[1] = hi64(b);
+  if (a.pair_stride != 0) {
+    const uint32_t odd = a.cls & 1u;
+#pragma unroll
+    for (int h = 0; h < V; ++h) {
+      const uint4 b = philox(
+          make_uint4(a.t, a.cls - odd, id - odd * a.pair_stride, (uint32_t)(q * V + h)), a.rk);
+      g[h] = odd ? hi64(b) : lo64(b);
+    }
   } else {
-    g[0] = half ? hi64(b) : lo64(b);
+    uint32_t c3, half;
+    if constexpr (V == 2) {
+      c3 = (uint32_t)q;
+      half = 0;
+    } else {
+      c3 = (uint32_t)(q >> 1);
+      half = (uint32_t)(q & 1);
+    }
+    const uint4 b = philox(make_uint4(a.t, a.cls, id, c3), a.rk);
+    if constexpr (V == 2) {
+      g[0] = lo64(b);
+      g[1] = hi64(b);
+    } else {
+      g[0] = half ? hi64(b) : lo64(b);
+    }
   }
   uint64_t sw[V];
   bool any = false;
@@ -180,6 +195,12 @@ cudaError_t launch_graph_class(const Planes& pl, const GraphDev& g, int64_t off,
   a.z = g.z;
   a.t = t;
   a.cls = cls;
+  a.pair_stride = 0;
+  if (g.cubic_L > 0) {
+    uint32_t s = 1;
+    for (uint32_t k = 0; k < cls / 8; ++k) s *= (uint32_t)g.cubic_L;
+    a.pair_stride = s;
+  }
   a.rk = rk;
   dim3 grid((unsigned)((count + 255) / 256), (unsigned)pl.P);
   return pl.V == 2 ? launch_v<2>(a, g.m, grid, s) : launch_v<1>(a, g.m, grid, s);
