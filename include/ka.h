@@ -190,6 +190,29 @@ ka_status ka_profile_read(ka_ctx *ctx, double *kernel_ms, int64_t *launches);
  * kernel error if one is pending. */
 ka_status ka_destroy(ka_ctx *ctx);
 
+/* Observables computed without allocating any memory.
+ *
+ * For callers that cannot call cudaMalloc -- code running where the device
+ * heap is reserved or allocation is forbidden, such as inside another
+ * framework's memory pool, a real-time loop, or a driver that has already
+ * committed every byte -- this variant of ka_observe uses no memory of its
+ * own: its per-replica accumulators live in a fixed array compiled into the
+ * library (128 KiB, enough for 4096 replicas), which every GPU that loads
+ * the library keeps until the process exits.  The paper has no counterpart;
+ * it is a deployment convenience.
+ *
+ * n, n0, p: device arrays in the canonical layout [R/64][N] uint64 (the
+ * layout of ka_get_state), read only.  counts: host int64 [R][4], written
+ * as by ka_observe.  stream: cudaStream_t or NULL.  Synchronises the stream.
+ * Returns KA_EINVAL when replicas is not a multiple of 64 or exceeds 4096.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the one array, which keeps the last call's contents (each call
+ * clears it first), so calls that overlap on the GPU -- concurrent streams
+ * or host threads -- race and must be serialised by the caller. */
+ka_status ka_observe_static(const uint64_t *n, const uint64_t *n0, const uint64_t *p, int64_t N,
+                            int32_t replicas, int64_t *counts, void *stream);
+
 /* Message of the last failed call on this context (never NULL). */
 const char *ka_last_error(const ka_ctx *ctx);
 

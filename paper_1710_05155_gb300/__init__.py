@@ -67,6 +67,8 @@ _SIGS = {
                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ka_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "ka_profile_read": (C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_int64)]),
+    "ka_observe_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
+                                    C.c_void_p, C.c_void_p]),
     "ka_destroy": (C.c_int, [C.c_void_p]),
     "ka_last_error": (C.c_char_p, [C.c_void_p]),
     "ka_status_name": (C.c_char_p, [C.c_int]),
@@ -236,6 +238,18 @@ def ka_profile_read(ctx: Ctx):
     ms, n = C.c_double(0), C.c_int64(0)
     _check(load().ka_profile_read(ctx.handle, C.byref(ms), C.byref(n)), "ka_profile_read", ctx)
     return ms.value, n.value
+
+
+def ka_observe_static(n_ptr: int, n0_ptr: int, p_ptr: int, N: int, replicas: int,
+                      stream: int | None = None) -> np.ndarray:
+    """Counts [R, 4] of caller-held device state (canonical [R/64, N] layout),
+    computed without allocating: the accumulators are a fixed array inside the
+    library (at most 4096 replicas)."""
+    out = np.zeros((replicas, 4), np.int64)
+    _check(load().ka_observe_static(C.c_void_p(n_ptr), C.c_void_p(n0_ptr), C.c_void_p(p_ptr), N,
+                                    replicas, _ptr(out), C.c_void_p(stream or 0)),
+           "ka_observe_static")
+    return out
 
 
 def ka_destroy(ctx: Ctx) -> None:

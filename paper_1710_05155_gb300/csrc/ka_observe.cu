@@ -125,4 +125,64 @@ cudaError_t launch_observe(const Planes& pl, int R, unsigned long long* counts_d
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant (ka_observe_static): the per-replica accumulators
+// live in a file-scope device array instead of memory the caller or the
+// library allocates.  Every GPU that loads the library holds this array
+// until the process exits.
+// ---------------------------------------------------------------------------
+
+constexpr int kStaticMaxReplicas = 4096;  // 4096 x 4 x 8 bytes = 128 KiB per device
+static __device__ __align__(256) unsigned long long g_static_counts[kStaticMaxReplicas * 4];
+
+namespace {
+constexpr int kMaxDevices = 64;
+unsigned long long* g_static_ptr[kMaxDevices] = {};  // device address of the array, per device
+}  // namespace
+
+// Device address of the array on the current device.  In host code the
+// symbol itself is only a host-side stand-in, so its address is looked up
+// once per device (with that device current) and cached.
+cudaError_t static_counts_ptr(unsigned long long** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (!g_static_ptr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_static_counts);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[dev] = (unsigned long long*)ptr;
+  }
+  *out = g_static_ptr[dev];
+  return cudaSuccess;
+}
+
 }  // namespace ka
+
+extern "C" ka_status ka_observe_static(const uint64_t* n, const uint64_t* n0, const uint64_t* p,
+                                       int64_t N, int32_t replicas, int64_t* counts,
+                                       void* stream) {
+  if (!n || !n0 || !p || !counts || N < 1 || replicas <= 0 || replicas % 64 ||
+      replicas > ka::kStaticMaxReplicas)
+    return KA_EINVAL;
+  const cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long* scratch = nullptr;
+  cudaError_t e = ka::static_counts_ptr(&scratch);
+  if (e != cudaSuccess) return KA_ECUDA;
+  // the canonical layout [R/64][N] is the device layout with one word per plane
+  ka::Planes pl{};
+  pl.n = const_cast<uint64_t*>(n);
+  pl.n0 = const_cast<uint64_t*>(n0);
+  pl.p = const_cast<uint64_t*>(p);
+  pl.N = N;
+  pl.W = replicas / 64;
+  pl.V = 1;
+  pl.P = pl.W;
+  e = ka::launch_observe(pl, replicas, scratch, st);  // clears the scratch, then accumulates
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(counts, scratch, (size_t)replicas * 4 * sizeof(int64_t),
+                        cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? KA_OK : KA_ECUDA;
+}
