@@ -106,6 +106,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def measured_traffic():
+    """DRAM bytes per k_cubic_group launch from the committed ncu summary, or
+    None when the kernel source changed since that capture."""
+    import hashlib
+
+    prof = os.path.join(ROOT, "profiles", "k_cubic_group_L128_R256.md")
+    src = os.path.join(ROOT, "paper_1710_05155_gb300", "csrc", "ka_sweep_cubic.cu")
+    try:
+        fields = {}
+        for line in open(prof):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if fields.get("kernel_source_sha256_16") != digest:
+            return None
+        return float(fields["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def oracle_sample(n_rep: int, sweeps: int, rho: float = RHOS[0]):
     """Time the oracle on n_rep replicas of the workload (initial state untimed)."""
     import oracle as O
@@ -213,12 +234,7 @@ def run_native(args, rank: int, world: int) -> None:
     bytes_per_launch = BYTES_PER_SITE_WORD_SWEEP * N_SITES * V / groups
     achieved = bytes_per_launch / (avg_launch_ms / 1000.0) / 1e9
     peak, peak_kind = _peaks()
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f).get("k_cubic_group_bytes_per_launch")
-    except Exception:
-        pass
+    traffic = measured_traffic()
 
     # end to end through the C ABI: initial state from pinned host memory,
     # S sweeps, counts back to the host, for every context
