@@ -190,6 +190,70 @@ ka_status ka_profile_read(ka_ctx *ctx, double *kernel_ms, int64_t *launches);
  * kernel error if one is pending. */
 ka_status ka_destroy(ka_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Batched and served execution
+ *
+ * A batch holds many independent jobs (each a context with its own
+ * topology, density, seed, replica count and sweep target) resident on one
+ * device, and advances them together: one kernel launch runs a bond-class
+ * group of every cubic job of the same shape class (d, words per plane, m),
+ * and one launch runs a colour class of every graph job of the same (words
+ * per plane, m).  Each job's result is bit-identical to running it alone:
+ * the random streams are keyed by the job's seed, sweep, class and site,
+ * never by its position in the batch.  The paper has no batching; this is
+ * the serving layer around its method.
+ * ------------------------------------------------------------------------ */
+typedef struct ka_batch ka_batch;
+
+typedef struct {
+    int64_t sweeps;        /* sweeps to run, >= 0 */
+    int64_t observe_every; /* observe after every this many sweeps (>= 1), and at the end */
+    uint64_t seed;         /* dynamics seed (ka_init) */
+    double rho;            /* density (ka_init) */
+} ka_job_spec;
+
+#define KA_BATCH_GRAPH 1 /* capture each round in a CUDA graph and replay it */
+#define KA_BATCH_PLAIN 2 /* run every job with its own launches (the unbatched reference) */
+
+/* Create a batch on `device` whose jobs may use at most hbm_budget bytes of
+ * device memory (contexts plus observation buffers).  All work is issued on
+ * `stream` (cudaStream_t or NULL). */
+ka_status ka_batch_create(int32_t device, void *stream, size_t hbm_budget, int32_t flags,
+                          ka_batch **out);
+
+/* Admit a job: allocates its context and observation buffer, builds its
+ * topology, draws its initial state and records the sweep-0 observation.
+ * KA_EBUSY (nothing allocated) when the job would exceed the budget. */
+ka_status ka_batch_add(ka_batch *b, const ka_params *params, const ka_job_spec *spec,
+                       int64_t *job_id);
+
+/* One round: advance every unfinished job by up to max_sweeps sweeps (a job
+ * stops early at its next observation point or its target), then record
+ * the due observations.  *sweeps_run = the round's length.  Synchronises. */
+ka_status ka_batch_step(ka_batch *b, int64_t max_sweeps, int64_t *sweeps_run);
+
+/* Time a few round lengths on the live batch (the rounds do real work) and
+ * keep the fastest for ka_batch_step(b, 0, ...).  *best_round may be NULL. */
+ka_status ka_batch_autotune(ka_batch *b, int64_t *best_round);
+
+/* Progress of a job. */
+ka_status ka_batch_poll(const ka_batch *b, int64_t job_id, int64_t *sweep, int32_t *finished);
+
+/* Observations of a job: *n_obs; if obs_sweeps / counts are non-NULL they
+ * receive the sweep of each observation [n_obs] and the counts
+ * [n_obs][R][4] (as ka_observe). */
+ka_status ka_batch_observations(const ka_batch *b, int64_t job_id, int64_t *n_obs,
+                                int64_t *obs_sweeps, int64_t *counts);
+
+/* Retire a job and free its memory (finished or not). */
+ka_status ka_batch_remove(ka_batch *b, int64_t job_id);
+
+/* Device bytes in use, jobs held, jobs still running. */
+ka_status ka_batch_info(const ka_batch *b, size_t *used_bytes, int64_t *jobs, int64_t *active);
+
+/* Free everything (NULL is fine). */
+ka_status ka_batch_destroy(ka_batch *b);
+
 /* Observables computed without allocating any memory.
  *
  * For callers that cannot call cudaMalloc -- code running where the device

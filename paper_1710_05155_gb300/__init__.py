@@ -36,6 +36,14 @@ class ka_params(C.Structure):
                 ("stream", C.c_void_p), ("device", C.c_int32), ("flags", C.c_int32)]
 
 
+class ka_job_spec(C.Structure):
+    _fields_ = [("sweeps", C.c_int64), ("observe_every", C.c_int64), ("seed", C.c_uint64),
+                ("rho", C.c_double)]
+
+
+KA_BATCH_GRAPH, KA_BATCH_PLAIN = 1, 2
+
+
 class ka_info_t(C.Structure):
     _fields_ = [("N", C.c_int64), ("z", C.c_int32), ("m", C.c_int32), ("replicas", C.c_int32),
                 ("words", C.c_int32), ("nclass", C.c_int64), ("nbonds", C.c_int64),
@@ -69,6 +77,16 @@ _SIGS = {
     "ka_profile_read": (C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_int64)]),
     "ka_observe_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                     C.c_void_p, C.c_void_p]),
+    "ka_batch_create": (C.c_int, [C.c_int32, C.c_void_p, C.c_size_t, C.c_int32, _P(C.c_void_p)]),
+    "ka_batch_add": (C.c_int, [C.c_void_p, _P(ka_params), _P(ka_job_spec), _P(C.c_int64)]),
+    "ka_batch_step": (C.c_int, [C.c_void_p, C.c_int64, _P(C.c_int64)]),
+    "ka_batch_autotune": (C.c_int, [C.c_void_p, _P(C.c_int64)]),
+    "ka_batch_poll": (C.c_int, [C.c_void_p, C.c_int64, _P(C.c_int64), _P(C.c_int32)]),
+    "ka_batch_observations": (C.c_int, [C.c_void_p, C.c_int64, _P(C.c_int64), C.c_void_p,
+                                        C.c_void_p]),
+    "ka_batch_remove": (C.c_int, [C.c_void_p, C.c_int64]),
+    "ka_batch_info": (C.c_int, [C.c_void_p, _P(C.c_size_t), _P(C.c_int64), _P(C.c_int64)]),
+    "ka_batch_destroy": (C.c_int, [C.c_void_p]),
     "ka_destroy": (C.c_int, [C.c_void_p]),
     "ka_last_error": (C.c_char_p, [C.c_void_p]),
     "ka_status_name": (C.c_char_p, [C.c_int]),
@@ -261,6 +279,74 @@ def ka_destroy(ctx: Ctx) -> None:
 
 def ka_last_error(ctx: Ctx) -> str:
     return load().ka_last_error(ctx.handle).decode()
+
+
+class Batch:
+    """Many independent jobs resident on one device, advanced together (batch API)."""
+
+    def __init__(self, device: int = 0, stream: int | None = None, hbm_budget: int = 150 << 30,
+                 flags: int = KA_BATCH_GRAPH):
+        h = C.c_void_p(0)
+        _check(load().ka_batch_create(device, C.c_void_p(stream or 0), hbm_budget, flags,
+                                      C.byref(h)), "ka_batch_create")
+        self.handle = h
+        self.device = device
+
+    def add(self, sweeps: int, observe_every: int, seed: int, rho: float, **params) -> int:
+        """Admit a job; returns its id.  Raises KaError(KA_EBUSY) when over budget."""
+        p, keep = make_params(device=self.device, **params)
+        spec = ka_job_spec(sweeps, observe_every, seed, rho)
+        jid = C.c_int64(0)
+        _check(load().ka_batch_add(self.handle, C.byref(p), C.byref(spec), C.byref(jid)),
+               "ka_batch_add")
+        return jid.value
+
+    def step(self, max_sweeps: int = 0) -> int:
+        ran = C.c_int64(0)
+        _check(load().ka_batch_step(self.handle, max_sweeps, C.byref(ran)), "ka_batch_step")
+        return ran.value
+
+    def autotune(self) -> int:
+        k = C.c_int64(0)
+        _check(load().ka_batch_autotune(self.handle, C.byref(k)), "ka_batch_autotune")
+        return k.value
+
+    def poll(self, job: int):
+        t, f = C.c_int64(0), C.c_int32(0)
+        _check(load().ka_batch_poll(self.handle, job, C.byref(t), C.byref(f)), "ka_batch_poll")
+        return t.value, bool(f.value)
+
+    def observations(self, job: int, replicas: int):
+        """(sweeps [n_obs], counts [n_obs, R, 4]) of a job."""
+        n = C.c_int64(0)
+        _check(load().ka_batch_observations(self.handle, job, C.byref(n), None, None),
+               "ka_batch_observations")
+        sw = np.zeros(n.value, np.int64)
+        cnt = np.zeros((n.value, replicas, 4), np.int64)
+        _check(load().ka_batch_observations(self.handle, job, C.byref(n), _ptr(sw), _ptr(cnt)),
+               "ka_batch_observations")
+        return sw, cnt
+
+    def remove(self, job: int) -> None:
+        _check(load().ka_batch_remove(self.handle, job), "ka_batch_remove")
+
+    def info(self):
+        used, jobs, active = C.c_size_t(0), C.c_int64(0), C.c_int64(0)
+        _check(load().ka_batch_info(self.handle, C.byref(used), C.byref(jobs), C.byref(active)),
+               "ka_batch_info")
+        return {"used_bytes": used.value, "jobs": jobs.value, "active": active.value}
+
+    def close(self) -> None:
+        if self.handle.value:
+            st = load().ka_batch_destroy(self.handle)
+            self.handle = C.c_void_p(0)
+            _check(st, "ka_batch_destroy")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Simulation:

@@ -9,36 +9,8 @@
 #include <string>
 #include <vector>
 
-#include "ka_internal.cuh"
+#include "ka_ctx.cuh"
 
-struct ka_ctx {
-  ka_params prm;
-  int topo = 0, d = 0, L = 0, z = 0, m = 0, R = 0;
-  int64_t N = 0, nclass = 0, nbonds = 0;
-  bool pencil = false;
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  bool owns = false;
-  void* buf = nullptr;
-  size_t bytes = 0;
-  ka::Planes pl{};
-  ka::InitScratch is{};
-  unsigned long long* counts_dev = nullptr;
-  uint64_t* stage = nullptr;
-  ka::GraphDev g{};
-  ka::Topology host;  // class offsets (graphs) and tables for inspection
-  bool initialized = false;
-  int64_t sweep = 0, K = -1;
-  uint64_t seed = 0;
-  ka::RoundKeys rk{};
-  std::string err;
-  // kernel timing
-  bool prof = false;
-  std::vector<cudaEvent_t> ev;
-  size_t ev_used = 0;
-  double prof_ms = 0.0;
-  int64_t prof_launches = 0;
-};
 
 namespace {
 
@@ -257,6 +229,18 @@ ka_status drain_profile(ka_ctx* c) {
 }
 
 }  // namespace
+
+namespace ka {
+ka_status create_context(const ka_params* params, void* buf, size_t bytes, bool owns, ka_ctx** out) {
+  return create_common(params, buf, bytes, owns, out);
+}
+ka_status context_bytes(const ka_params* params, size_t* bytes) {
+  Shape s{};
+  if (!bytes || check_params(params, s)) return KA_EINVAL;
+  *bytes = layout_of(s).total;
+  return KA_OK;
+}
+}  // namespace ka
 
 extern "C" {
 

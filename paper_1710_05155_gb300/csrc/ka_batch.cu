@@ -1,0 +1,575 @@
+// ka_batch.cu -- many independent jobs advanced together (include/ka.h, batch API).
+//
+// Every job is an ordinary context (own device buffer, topology, seed,
+// density, replica count) plus a device buffer of observations.  A round
+// advances all unfinished jobs by up to k sweeps: for every sweep offset s
+// and every bond-class group, ONE launch of the pencil kernel covers all
+// cubic work units (job planes) of a shape class (d, V, m), and ONE launch of
+// the edge-gather kernel covers class c of all graph units of a shape class
+// (V, m).  Units carry their own sweep counter t_base and stop counter t_end
+// in a device table, so a job that reaches its next observation point (or
+// its target) inside the round simply idles.  The round's launch sequence
+// can be captured in a CUDA graph and replayed while the job set and the
+// round length stay the same (the unit tables are refreshed by a copy before
+// every replay).
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "ka_ctx.cuh"
+
+namespace {
+
+struct Job {
+  int64_t id = 0;
+  ka_ctx* ctx = nullptr;
+  void* buf = nullptr;
+  size_t bytes = 0;
+  int64_t target = 0, every = 1, t = 0;
+  int64_t n_obs = 0, cap = 0;
+  int64_t* obs_dev = nullptr;  // [cap][R][4]
+  std::vector<int64_t> obs_t;
+  bool finished = false;
+  bool batched = true;  // false: cubic lattice on the edge-gather path, run with its own launches
+};
+
+struct CubicClass {
+  int d = 0, V = 0, m = 0;
+  std::vector<ka::CubicUnit> units;
+  std::vector<Job*> owner;
+  ka::CubicUnit* dev = nullptr;
+  uint32_t ntiles[2] = {0, 0};
+  int PSmax = 0;
+};
+
+struct GraphClass {
+  int V = 0, m = 0, cmax = 0;
+  std::vector<ka::GraphUnit> units;
+  std::vector<Job*> owner;
+  std::vector<int64_t> prefix, first, total;  // per class: [cmax][n+1], [cmax][n], [cmax]
+  ka::GraphUnit* dev = nullptr;
+  int64_t* prefix_dev = nullptr;
+  int64_t* first_dev = nullptr;
+};
+
+uint32_t cubic_tiles(int d, int L, int V, bool x) {
+  const int tp = 8 / V, win = 16 / V;
+  int64_t np = 1;
+  for (int k = 0; k < d - 1; ++k) np *= L;
+  if (d >= 2) np /= 2;
+  if (x) return (uint32_t)((np + tp - 1) / tp);
+  int64_t t = (L + win - 1) / win;
+  for (int k = 0; k < d - 2; ++k) t *= L;
+  return (uint32_t)t;
+}
+
+}  // namespace
+
+struct ka_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t budget = 0, used = 0;
+  int32_t flags = 0;
+  int64_t next_id = 1;
+  std::map<int64_t, Job*> jobs;
+  bool dirty = true;
+  std::vector<CubicClass> cubic;
+  std::vector<GraphClass> graph;
+  std::vector<void*> table_mem;  // device tables of the current job set
+  bool own_stream = false;
+  cudaGraphExec_t exec = nullptr;
+  int64_t exec_k = 0;
+  int64_t last_k = 0;  // a round length is captured the second time it is used
+  int64_t tuned_k = 16;
+  std::string err;
+};
+
+namespace {
+
+ka_status cuda_err(ka_batch* b, cudaError_t e, const char* what) {
+  b->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return KA_ECUDA;
+}
+
+void free_tables(ka_batch* b) {
+  for (void* p : b->table_mem) cudaFree(p);
+  b->table_mem.clear();
+  b->cubic.clear();
+  b->graph.clear();
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  b->exec_k = 0;
+}
+
+template <typename T>
+cudaError_t dev_alloc(ka_batch* b, T** p, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e == cudaSuccess) b->table_mem.push_back((void*)*p);
+  return e;
+}
+
+// Group the unfinished batched jobs into shape classes and build the unit
+// tables (host copies; device copies are allocated here and filled per round).
+cudaError_t rebuild(ka_batch* b) {
+  free_tables(b);
+  for (auto& kv : b->jobs) {
+    Job* j = kv.second;
+    if (j->finished || !j->batched) continue;
+    ka_ctx* c = j->ctx;
+    const int V = c->pl.V;
+    for (int q = 0; q < c->pl.P; ++q) {
+      uint64_t* n = c->pl.n + (size_t)q * c->pl.plane_elems();
+      uint64_t* p = c->pl.p + (size_t)q * c->pl.plane_elems();
+      if (c->topo == KA_CUBIC) {
+        CubicClass* cc = nullptr;
+        for (auto& x : b->cubic)
+          if (x.d == c->d && x.V == V && x.m == c->m) cc = &x;
+        if (!cc) {
+          b->cubic.push_back(CubicClass{});
+          cc = &b->cubic.back();
+          cc->d = c->d;
+          cc->V = V;
+          cc->m = c->m;
+        }
+        ka::CubicUnit u{};
+        u.n = n;
+        u.p = p;
+        u.d = c->d;
+        u.L = c->L;
+        u.word0 = (uint32_t)(q * V);
+        u.tile0[0] = cc->ntiles[0];
+        u.tile0[1] = cc->ntiles[1];
+        cc->ntiles[0] += cubic_tiles(c->d, c->L, V, true);
+        cc->ntiles[1] += cubic_tiles(c->d, c->L, V, false);
+        u.rk = c->rk;
+        cc->PSmax = std::max(cc->PSmax, ((c->L + 15) / 16) * 16 + 1);
+        cc->units.push_back(u);
+        cc->owner.push_back(j);
+      } else {
+        GraphClass* gc = nullptr;
+        for (auto& x : b->graph)
+          if (x.V == V && x.m == c->m) gc = &x;
+        if (!gc) {
+          b->graph.push_back(GraphClass{});
+          gc = &b->graph.back();
+          gc->V = V;
+          gc->m = c->m;
+        }
+        ka::GraphUnit u{};
+        u.n = n;
+        u.p = p;
+        u.nbr = c->g.nbr;
+        u.bu = c->g.bu;
+        u.bv = c->g.bv;
+        u.bid = c->g.bid;
+        u.z = c->z;
+        u.word0 = (uint32_t)(q * V);
+        u.rk = c->rk;
+        gc->units.push_back(u);
+        gc->owner.push_back(j);
+        gc->cmax = std::max<int>(gc->cmax, (int)c->nclass);
+      }
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  for (auto& cc : b->cubic) {
+    if ((e = dev_alloc(b, &cc.dev, cc.units.size()))) return e;
+  }
+  for (auto& gc : b->graph) {
+    const int n = (int)gc.units.size();
+    gc.prefix.assign((size_t)gc.cmax * (n + 1), 0);
+    gc.first.assign((size_t)gc.cmax * n, 0);
+    gc.total.assign(gc.cmax, 0);
+    for (int c = 0; c < gc.cmax; ++c) {
+      int64_t acc = 0;
+      for (int u = 0; u < n; ++u) {
+        const ka_ctx* x = gc.owner[u]->ctx;
+        int64_t cnt = 0, f = 0;
+        if (c < x->nclass) {
+          f = x->host.class_off[c];
+          cnt = x->host.class_off[c + 1] - f;
+        }
+        gc.prefix[(size_t)c * (n + 1) + u] = acc;
+        gc.first[(size_t)c * n + u] = f;
+        acc += cnt;
+      }
+      gc.prefix[(size_t)c * (n + 1) + n] = acc;
+      gc.total[c] = acc;
+    }
+    if ((e = dev_alloc(b, &gc.dev, gc.units.size()))) return e;
+    if ((e = dev_alloc(b, &gc.prefix_dev, gc.prefix.size()))) return e;
+    if ((e = dev_alloc(b, &gc.first_dev, gc.first.size()))) return e;
+    e = cudaMemcpyAsync(gc.prefix_dev, gc.prefix.data(), gc.prefix.size() * sizeof(int64_t),
+                        cudaMemcpyHostToDevice, b->stream);
+    if (!e) e = cudaMemcpyAsync(gc.first_dev, gc.first.data(), gc.first.size() * sizeof(int64_t),
+                                cudaMemcpyHostToDevice, b->stream);
+    if (e) return e;
+  }
+  b->dirty = false;
+  b->last_k = 0;
+  return cudaStreamSynchronize(b->stream);
+}
+
+// sweeps job j may run in a round of length k: up to its next observation or its target
+int64_t allowance(const Job* j, int64_t k) {
+  const int64_t next_obs = (j->t / j->every + 1) * j->every;
+  const int64_t stop = std::min(next_obs, j->target);
+  return std::max<int64_t>(0, std::min(k, stop - j->t));
+}
+
+// The launches of one round of length k (captured or run directly).
+cudaError_t issue_round(ka_batch* b, int64_t k) {
+  cudaError_t e = cudaSuccess;
+  for (int64_t s = 0; s < k && !e; ++s) {
+    for (auto& cc : b->cubic) {
+      const int npar = (cc.d == 1) ? 1 : 2;
+      for (int mu = 0; mu < cc.d && !e; ++mu)
+        for (int par = 0; par < npar && !e; ++par) {
+          const bool x = (mu == 0) || cc.d == 1;
+          e = ka::launch_cubic_group_batch(cc.dev, (int)cc.units.size(), cc.ntiles[x ? 0 : 1],
+                                           cc.PSmax, cc.d, cc.V, cc.m, mu, par, (uint32_t)s,
+                                           b->stream);
+        }
+    }
+    for (auto& gc : b->graph) {
+      const int n = (int)gc.units.size();
+      for (int c = 0; c < gc.cmax && !e; ++c)
+        e = ka::launch_graph_class_batch(gc.dev, gc.prefix_dev + (size_t)c * (n + 1),
+                                         gc.first_dev + (size_t)c * n, n, gc.total[c], gc.V, gc.m,
+                                         (uint32_t)c, (uint32_t)s, b->stream);
+    }
+  }
+  return e;
+}
+
+ka_status observe_job(ka_batch* b, Job* j) {
+  if (j->n_obs >= j->cap) {
+    b->err = "observation buffer full";
+    return KA_ESTATE;
+  }
+  const int R = j->ctx->R;
+  cudaError_t e = ka::launch_observe(j->ctx->pl, R,
+                                     (unsigned long long*)(j->obs_dev + j->n_obs * R * 4),
+                                     b->stream);
+  if (e) return cuda_err(b, e, "observe");
+  j->obs_t.push_back(j->t);
+  j->n_obs++;
+  return KA_OK;
+}
+
+ka_status run_round(ka_batch* b, int64_t k_req, int64_t* ran) {
+  if (b->dirty) {
+    cudaError_t e = rebuild(b);
+    if (e) return cuda_err(b, e, "batch tables");
+  }
+  // the round's length: the requested k, but no longer than any job may go
+  int64_t k = 0;
+  for (auto& kv : b->jobs) {
+    Job* j = kv.second;
+    if (!j->finished) k = std::max(k, allowance(j, k_req));
+  }
+  if (ran) *ran = k;
+  if (k == 0) return KA_OK;
+  cudaError_t e = cudaSuccess;
+  if (b->flags & KA_BATCH_PLAIN) {
+    // the unbatched reference: every job with its own launches
+    for (auto& kv : b->jobs) {
+      Job* j = kv.second;
+      if (j->finished) continue;
+      ka_status st = ka_sweep(j->ctx, allowance(j, k));
+      if (st) return st;
+    }
+  } else {
+    // unit tables: this round's start and stop sweeps
+    for (auto& cc : b->cubic) {
+      for (size_t u = 0; u < cc.units.size(); ++u) {
+        const Job* j = cc.owner[u];
+        cc.units[u].t_base = (uint32_t)j->t;
+        cc.units[u].t_end = (uint32_t)(j->t + allowance(j, k));
+      }
+      if ((e = cudaMemcpyAsync(cc.dev, cc.units.data(), cc.units.size() * sizeof(ka::CubicUnit),
+                               cudaMemcpyHostToDevice, b->stream)))
+        return cuda_err(b, e, "unit table");
+    }
+    for (auto& gc : b->graph) {
+      for (size_t u = 0; u < gc.units.size(); ++u) {
+        const Job* j = gc.owner[u];
+        gc.units[u].t_base = (uint32_t)j->t;
+        gc.units[u].t_end = (uint32_t)(j->t + allowance(j, k));
+      }
+      if ((e = cudaMemcpyAsync(gc.dev, gc.units.data(), gc.units.size() * sizeof(ka::GraphUnit),
+                               cudaMemcpyHostToDevice, b->stream)))
+        return cuda_err(b, e, "unit table");
+    }
+    const bool replay = (b->flags & KA_BATCH_GRAPH) && k == b->last_k;
+    b->last_k = k;
+    if (replay) {
+      if (!b->exec || b->exec_k != k) {
+        if (b->exec) {
+          cudaGraphExecDestroy(b->exec);
+          b->exec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        if (!e) {
+          const cudaError_t ei = issue_round(b, k);
+          e = cudaStreamEndCapture(b->stream, &g);
+          if (!e) e = ei;
+        }
+        if (!e) e = cudaGraphInstantiate(&b->exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e) return cuda_err(b, e, "round graph");
+        b->exec_k = k;
+      }
+      e = cudaGraphLaunch(b->exec, b->stream);
+    } else {
+      e = issue_round(b, k);
+    }
+    if (e) return cuda_err(b, e, "round");
+    // jobs on the edge-gather path of a cubic lattice run with their own launches
+    for (auto& kv : b->jobs) {
+      Job* j = kv.second;
+      if (j->finished || j->batched) continue;
+      ka_status st = ka_sweep(j->ctx, allowance(j, k));
+      if (st) return st;
+    }
+  }
+  // advance the counters, record due observations, retire finished jobs
+  for (auto& kv : b->jobs) {
+    Job* j = kv.second;
+    if (j->finished) continue;
+    const int64_t a = allowance(j, k);
+    if (a == 0) continue;
+    j->t += a;
+    if (!(b->flags & KA_BATCH_PLAIN) && j->batched) j->ctx->sweep = j->t;
+    if (j->t % j->every == 0 || j->t == j->target) {
+      ka_status st = observe_job(b, j);
+      if (st) return st;
+    }
+    if (j->t >= j->target) {
+      j->finished = true;
+      b->dirty = true;
+    }
+  }
+  e = cudaStreamSynchronize(b->stream);
+  if (e) return cuda_err(b, e, "round sync");
+  return KA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ka_status ka_batch_create(int32_t device, void* stream, size_t hbm_budget, int32_t flags,
+                          ka_batch** out) {
+  if (!out) return KA_EINVAL;
+  *out = nullptr;
+  ka_batch* b = new ka_batch();
+  b->device = device;
+  b->stream = (cudaStream_t)stream;
+  if (!b->stream) {  // stream capture needs a stream other than the legacy default one
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    const cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (prev >= 0) cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+      delete b;
+      return KA_ECUDA;
+    }
+    b->own_stream = true;
+  }
+  b->budget = hbm_budget;
+  b->flags = flags;
+  *out = b;
+  return KA_OK;
+}
+
+ka_status ka_batch_add(ka_batch* b, const ka_params* params, const ka_job_spec* spec,
+                       int64_t* job_id) {
+  if (!b || !params || !spec || spec->sweeps < 0 || spec->observe_every < 1) return KA_EINVAL;
+  if (spec->sweeps >= ((int64_t)1 << 32)) return KA_EINVAL;
+  ka_params prm = *params;
+  prm.device = b->device;
+  prm.stream = b->stream;
+  size_t bytes = 0;
+  ka_status st = ka::context_bytes(&prm, &bytes);
+  if (st) return st;
+  const int64_t cap = spec->sweeps / spec->observe_every + 2;
+  const size_t obs_bytes = (size_t)cap * prm.replicas * 4 * sizeof(int64_t);
+  const size_t need = bytes + obs_bytes;
+  if (b->used + need > b->budget) return KA_EBUSY;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->device);
+  Job* j = new Job();
+  cudaError_t e = cudaMalloc(&j->buf, bytes);
+  if (!e) e = cudaMalloc((void**)&j->obs_dev, obs_bytes);
+  if (e) {
+    cudaGetLastError();
+    cudaFree(j->buf);
+    delete j;
+    if (prev >= 0) cudaSetDevice(prev);
+    return KA_ENOMEM;
+  }
+  st = ka::create_context(&prm, j->buf, bytes, true, &j->ctx);
+  if (!st) st = ka_init(j->ctx, spec->seed, spec->rho);
+  if (st) {
+    if (j->ctx)
+      ka_destroy(j->ctx);
+    else
+      cudaFree(j->buf);
+    cudaFree(j->obs_dev);
+    delete j;
+    if (prev >= 0) cudaSetDevice(prev);
+    return st;
+  }
+  j->id = b->next_id++;
+  j->bytes = need;
+  j->target = spec->sweeps;
+  j->every = spec->observe_every;
+  j->cap = cap;
+  j->batched = !(j->ctx->topo == KA_CUBIC && !j->ctx->pencil);
+  st = observe_job(b, j);  // sweep 0
+  if (j->target == 0) j->finished = true;
+  b->jobs[j->id] = j;
+  b->used += need;
+  b->dirty = true;
+  if (prev >= 0) cudaSetDevice(prev);
+  if (job_id) *job_id = j->id;
+  return st;
+}
+
+ka_status ka_batch_step(ka_batch* b, int64_t max_sweeps, int64_t* sweeps_run) {
+  if (!b || max_sweeps < 0) return KA_EINVAL;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->device);
+  const ka_status st = run_round(b, max_sweeps ? max_sweeps : b->tuned_k, sweeps_run);
+  if (prev >= 0) cudaSetDevice(prev);
+  return st;
+}
+
+ka_status ka_batch_autotune(ka_batch* b, int64_t* best_round) {
+  if (!b) return KA_EINVAL;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->device);
+  const int64_t cand[] = {4, 16, 64};
+  double best = -1.0;
+  int64_t best_k = b->tuned_k;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  ka_status st = KA_OK;
+  for (int64_t k : cand) {
+    // work of this round: site-words times sweeps over the unfinished jobs
+    double work = 0.0;
+    for (auto& kv : b->jobs) {
+      const Job* j = kv.second;
+      if (!j->finished) work += (double)j->ctx->N * (j->ctx->R / 64) * (double)allowance(j, k);
+    }
+    if (work == 0.0) break;
+    if (b->dirty) {  // table rebuild outside the timed region
+      cudaError_t e = rebuild(b);
+      if (e) {
+        st = cuda_err(b, e, "batch tables");
+        break;
+      }
+    }
+    cudaEventRecord(e0, b->stream);
+    int64_t ran = 0;
+    st = run_round(b, k, &ran);
+    cudaEventRecord(e1, b->stream);
+    cudaEventSynchronize(e1);
+    if (st) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double rate = work / (ms > 0.f ? ms : 1e-3f);
+    if (rate > best) {
+      best = rate;
+      best_k = k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->tuned_k = best_k;
+  if (best_round) *best_round = best_k;
+  if (prev >= 0) cudaSetDevice(prev);
+  return st;
+}
+
+ka_status ka_batch_poll(const ka_batch* b, int64_t job_id, int64_t* sweep, int32_t* finished) {
+  if (!b) return KA_EINVAL;
+  auto it = b->jobs.find(job_id);
+  if (it == b->jobs.end()) return KA_EINVAL;
+  if (sweep) *sweep = it->second->t;
+  if (finished) *finished = it->second->finished ? 1 : 0;
+  return KA_OK;
+}
+
+ka_status ka_batch_observations(const ka_batch* b, int64_t job_id, int64_t* n_obs,
+                                int64_t* obs_sweeps, int64_t* counts) {
+  if (!b) return KA_EINVAL;
+  auto it = b->jobs.find(job_id);
+  if (it == b->jobs.end()) return KA_EINVAL;
+  const Job* j = it->second;
+  if (n_obs) *n_obs = j->n_obs;
+  if (obs_sweeps) std::memcpy(obs_sweeps, j->obs_t.data(), j->obs_t.size() * sizeof(int64_t));
+  if (counts && j->n_obs > 0) {
+    cudaError_t e = cudaMemcpyAsync(counts, j->obs_dev,
+                                    (size_t)j->n_obs * j->ctx->R * 4 * sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, b->stream);
+    if (!e) e = cudaStreamSynchronize(b->stream);
+    if (e) return KA_ECUDA;
+  }
+  return KA_OK;
+}
+
+ka_status ka_batch_remove(ka_batch* b, int64_t job_id) {
+  if (!b) return KA_EINVAL;
+  auto it = b->jobs.find(job_id);
+  if (it == b->jobs.end()) return KA_EINVAL;
+  Job* j = it->second;
+  cudaStreamSynchronize(b->stream);
+  const ka_status st = ka_destroy(j->ctx);  // frees the context's buffer
+  cudaFree(j->obs_dev);
+  b->used -= j->bytes;
+  b->jobs.erase(it);
+  delete j;
+  b->dirty = true;
+  return st;
+}
+
+ka_status ka_batch_info(const ka_batch* b, size_t* used_bytes, int64_t* jobs, int64_t* active) {
+  if (!b) return KA_EINVAL;
+  int64_t a = 0;
+  for (auto& kv : b->jobs) a += kv.second->finished ? 0 : 1;
+  if (used_bytes) *used_bytes = b->used;
+  if (jobs) *jobs = (int64_t)b->jobs.size();
+  if (active) *active = a;
+  return KA_OK;
+}
+
+ka_status ka_batch_destroy(ka_batch* b) {
+  if (!b) return KA_OK;
+  cudaStreamSynchronize(b->stream);
+  ka_status st = KA_OK;
+  for (auto& kv : b->jobs) {
+    Job* j = kv.second;
+    if (ka_destroy(j->ctx)) st = KA_ECUDA;
+    cudaFree(j->obs_dev);
+    delete j;
+  }
+  free_tables(b);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,10 @@
+// ka_cubic_d1_batch.cu -- the batched cubic kernels of dimension 1.
+#define KA_CUBIC_INSTANCES
+#include "ka_cubic_kernel.cuh"
+
+namespace ka {
+namespace cubic {
+template cudaError_t launch_d<1, true>(int, bool, const GroupArgs&, const BatchArgs&, int,
+                                          unsigned, size_t, cudaStream_t);
+}  // namespace cubic
+}  // namespace ka

@@ -97,6 +97,35 @@ struct CubicShape {
   int d, L, m;
 };
 
+// One work unit of a batched launch: one state plane of one instance.  Its
+// sweep counter t_base lives in device memory; a launch runs sweep
+// t_base + sweep offset of every unit whose counter is still below t_end.
+struct CubicUnit {
+  uint64_t* n;
+  uint64_t* p;
+  int d, L;
+  uint32_t word0;
+  uint32_t tile0[2];  // first global tile of this unit: [0] mu = 0, [1] mu > 0
+  uint32_t t_base, t_end;
+  RoundKeys rk;
+};
+
+// Launch-wide arguments of a batched group launch.
+struct BatchArgs {
+  CubicUnit* units;
+  int nunits;
+  int mu, par;
+  uint32_t ntiles;  // all tiles of all units for this mu
+  uint32_t sweep_offset;
+  int PSmax;        // largest pencil stride (shared-memory sizing)
+};
+
+// Group (mu, par) of sweep t_base + sweep_offset for every unit of a batch
+// (all units share d, V and m); ntiles = sum of the units' tiles for this mu.
+cudaError_t launch_cubic_group_batch(CubicUnit* units_dev, int nunits, uint32_t ntiles, int PSmax,
+                                     int d, int V, int m, int mu, int par, uint32_t sweep_offset,
+                                     cudaStream_t st);
+
 // One group (mu, par) of four classes on plane q, sweep index t.
 cudaError_t launch_cubic_group(const Planes& pl, int q, const CubicShape& s, int mu, int par,
                                uint32_t t, const RoundKeys& rk, cudaStream_t st);
@@ -112,6 +141,25 @@ struct GraphDev {
 // Class c (bonds [off, off + count) of the class-ordered bond arrays), all planes.
 cudaError_t launch_graph_class(const Planes& pl, const GraphDev& g, int64_t off, int64_t count,
                                uint32_t cls, uint32_t t, const RoundKeys& rk, cudaStream_t st);
+
+// One graph work unit of a batched launch: one state plane of one job.
+struct GraphUnit {
+  uint64_t* n;
+  uint64_t* p;
+  const int32_t* nbr;
+  const int32_t* bu;
+  const int32_t* bv;
+  const uint32_t* bid;
+  int z;
+  uint32_t word0;  // global index of the plane's first word
+  uint32_t t_base, t_end;
+  RoundKeys rk;
+};
+// Class cls of sweep t_base + sweep_offset for every unit (all share V and m).
+cudaError_t launch_graph_class_batch(const GraphUnit* units_dev, const int64_t* prefix_dev,
+                                     const int64_t* first_dev, int nunits, int64_t total_edges,
+                                     int V, int m, uint32_t cls, uint32_t sweep_offset,
+                                     cudaStream_t s);
 
 struct InitScratch {
   uint32_t* hist;      // [R][256]

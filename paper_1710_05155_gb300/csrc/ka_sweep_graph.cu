@@ -178,7 +178,111 @@ cudaError_t launch_v(const ClassArgs& a, int m, dim3 grid, cudaStream_t s) {
   }
 }
 
+// Batched form: one launch runs class c of every graph unit (one state plane
+// of one job); edges of all units are numbered consecutively, unit u owning
+// [prefix[u], prefix[u+1]) of them, which start at edge first[u] of its
+// class-ordered edge arrays.  Units whose sweep counter reached t_end skip.
+template <int V, int M>
+__global__ void __launch_bounds__(256) k_graph_class_batch(const GraphUnit* __restrict__ units,
+                                                           const int64_t* __restrict__ prefix,
+                                                           const int64_t* __restrict__ first,
+                                                           int nunits, uint32_t cls,
+                                                           uint32_t sweep_offset) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= prefix[nunits]) return;
+  int lo = 0, hi = nunits - 1;  // last unit with prefix <= e
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= e) lo = mid; else hi = mid - 1;
+  }
+  const GraphUnit& gu = units[lo];
+  const uint32_t t = gu.t_base + sweep_offset;
+  if (t >= gu.t_end) return;
+  const int64_t k = first[lo] + (e - prefix[lo]);
+  uint64_t* np = gu.n;
+  uint64_t* pp = gu.p;
+  const int32_t u = gu.bu[k], v = gu.bv[k];
+  const uint32_t id = gu.bid[k];
+  const int z = gu.z;
+  uint64_t nu[V], nv[V];
+  ld<V>(np, u, nu);
+  ld<V>(np, v, nv);
+  uint64_t cu2[V], cu1[V], cu0[V], cv2[V], cv1[V], cv0[V];
+#pragma unroll
+  for (int h = 0; h < V; ++h) cu2[h] = cu1[h] = cu0[h] = cv2[h] = cv1[h] = cv0[h] = 0;
+  for (int q = 0; q < z; ++q) {
+    const int32_t wu = gu.nbr[(int64_t)u * z + q];
+    const int32_t wv = gu.nbr[(int64_t)v * z + q];
+    uint64_t xu[V], xv[V];
+    ld<V>(np, wu, xu);
+    ld<V>(np, wv, xv);
+    const uint64_t keep_u = (wu != v) ? ~0ull : 0ull;
+    const uint64_t keep_v = (wv != u) ? ~0ull : 0ull;
+#pragma unroll
+    for (int h = 0; h < V; ++h) {
+      add3(cu2[h], cu1[h], cu0[h], xu[h] & keep_u);
+      add3(cv2[h], cv1[h], cv0[h], xv[h] & keep_v);
+    }
+  }
+  // graph gate stream: block (t, class, edge, word pair), half = word parity
+  uint64_t g[V];
+  const uint32_t w0 = gu.word0;
+  if constexpr (V == 2) {
+    const uint4 b = philox(make_uint4(t, cls, id, w0 >> 1), gu.rk);
+    g[0] = lo64(b);
+    g[1] = hi64(b);
+  } else {
+    const uint4 b = philox(make_uint4(t, cls, id, w0 >> 1), gu.rk);
+    g[0] = (w0 & 1u) ? hi64(b) : lo64(b);
+  }
+  uint64_t sw[V];
+  bool any = false;
+#pragma unroll
+  for (int h = 0; h < V; ++h) {
+    const uint64_t ok = le3<M>(cu2[h], cu1[h], cu0[h]) & le3<M>(cv2[h], cv1[h], cv0[h]);
+    sw[h] = (nu[h] ^ nv[h]) & g[h] & ok;
+    nu[h] ^= sw[h];
+    nv[h] ^= sw[h];
+    any |= (sw[h] != 0);
+  }
+  if (any) {
+    st<V>(np, u, nu);
+    st<V>(np, v, nv);
+    uint64_t pu[V], pv[V];
+    ld<V>(pp, u, pu);
+    ld<V>(pp, v, pv);
+#pragma unroll
+    for (int h = 0; h < V; ++h) {
+      pu[h] &= ~sw[h];
+      pv[h] &= ~sw[h];
+    }
+    st<V>(pp, u, pu);
+    st<V>(pp, v, pv);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_graph_class_batch(const GraphUnit* units_dev, const int64_t* prefix_dev,
+                                     const int64_t* first_dev, int nunits, int64_t total_edges,
+                                     int V, int m, uint32_t cls, uint32_t sweep_offset,
+                                     cudaStream_t s) {
+  if (nunits <= 0 || total_edges <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((total_edges + 255) / 256);
+  const int mm = m < 7 ? m : 7;
+#define KA_CASE(VV, MM)                                                                  \
+  if (V == VV && mm == MM) {                                                             \
+    k_graph_class_batch<VV, MM><<<grid, 256, 0, s>>>(units_dev, prefix_dev, first_dev,   \
+                                                     nunits, cls, sweep_offset);         \
+    return cudaGetLastError();                                                           \
+  }
+  KA_CASE(1, 0) KA_CASE(1, 1) KA_CASE(1, 2) KA_CASE(1, 3) KA_CASE(1, 4) KA_CASE(1, 5)
+  KA_CASE(1, 6) KA_CASE(1, 7)
+  KA_CASE(2, 0) KA_CASE(2, 1) KA_CASE(2, 2) KA_CASE(2, 3) KA_CASE(2, 4) KA_CASE(2, 5)
+  KA_CASE(2, 6) KA_CASE(2, 7)
+#undef KA_CASE
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_graph_class(const Planes& pl, const GraphDev& g, int64_t off, int64_t count,
                                uint32_t cls, uint32_t t, const RoundKeys& rk, cudaStream_t s) {

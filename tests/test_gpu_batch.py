@@ -1,0 +1,110 @@
+"""Batched execution: every job gives the same result alone and in the mix.
+
+A batch advances many jobs of uneven size and type together (one launch per
+bond-class group for all cubic jobs of a shape class, one per colour class for
+all graph jobs); the random streams are keyed by each job's own seed, sweep,
+class and site, so each job's observations must equal, bit for bit, those of
+the same job run alone through a plain context -- which the parity tests tie
+to the oracle.  Also: admission by memory budget, removal, autotuning.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU-only hosts
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1710_05155_gb300 as K  # noqa: E402
+
+JOBS = [
+    dict(params=dict(topo=K.KA_CUBIC, d=3, L=16, m=3, replicas=64), sweeps=37, every=10, seed=5, rho=0.75),
+    dict(params=dict(topo=K.KA_CUBIC, d=3, L=24, m=3, replicas=64), sweeps=20, every=7, seed=6, rho=0.80),
+    dict(params=dict(topo=K.KA_CUBIC, d=3, L=32, m=3, replicas=256), sweeps=25, every=25, seed=7, rho=0.85),
+    dict(params=dict(topo=K.KA_CUBIC, d=3, L=20, m=2, replicas=128), sweeps=12, every=5, seed=8, rho=0.6),
+    dict(params=dict(topo=K.KA_CUBIC, d=2, L=16, m=1, replicas=192), sweeps=9, every=4, seed=9, rho=0.5),
+    dict(params=dict(topo=K.KA_RRG, N=4096, z=4, m=2, replicas=64, graph_seed=1), sweeps=30, every=10, seed=10, rho=0.78),
+    dict(params=dict(topo=K.KA_RRG, N=2048, z=4, m=2, replicas=128, graph_seed=2), sweeps=17, every=6, seed=11, rho=0.82),
+    dict(params=dict(topo=K.KA_RRG, N=1000, z=3, m=1, replicas=64, graph_seed=3), sweeps=14, every=14, seed=12, rho=0.7),
+    dict(params=dict(topo=K.KA_CUBIC, d=3, L=8, m=3, replicas=64, flags=K.KA_FLAG_GENERIC), sweeps=11, every=3, seed=13, rho=0.7),
+]
+
+
+def _alone(job):
+    sim = K.Simulation(**job["params"])
+    sim.init(job["seed"], job["rho"])
+    sweeps, counts = [], []
+    t, c = sim.observe()
+    sweeps.append(t)
+    counts.append(c.copy())
+    while t < job["sweeps"]:
+        step = min(job["every"] - t % job["every"], job["sweeps"] - t)
+        sim.sweep(step)
+        t, c = sim.observe()
+        sweeps.append(t)
+        counts.append(c.copy())
+    sim.close()
+    return np.array(sweeps), np.stack(counts)
+
+
+@pytest.mark.parametrize("flags,k", [(K.KA_BATCH_GRAPH, 8), (0, 5), (K.KA_BATCH_PLAIN, 6),
+                                     (K.KA_BATCH_GRAPH, 1)])
+def test_jobs_alone_equal_jobs_in_the_mix(flags, k):
+    with K.Batch(flags=flags) as b:
+        ids = [b.add(j["sweeps"], j["every"], j["seed"], j["rho"], **j["params"]) for j in JOBS]
+        for _ in range(1000):
+            if b.info()["active"] == 0:
+                break
+            b.step(k)
+        assert b.info()["active"] == 0
+        for jid, job in zip(ids, JOBS):
+            t, done = b.poll(jid)
+            assert done and t == job["sweeps"]
+            sw, cnt = b.observations(jid, job["params"]["replicas"])
+            want_sw, want_cnt = _alone(job)
+            assert (sw == want_sw).all()
+            assert (cnt == want_cnt).all(), f"job {jid} differs from its solo run"
+
+
+def test_jobs_joining_a_running_batch():
+    # continuous batching: a job admitted while others are mid-run still
+    # matches its solo run
+    with K.Batch() as b:
+        first = [b.add(j["sweeps"], j["every"], j["seed"], j["rho"], **j["params"]) for j in JOBS[:4]]
+        b.step(6)
+        b.step(6)
+        late = [b.add(j["sweeps"], j["every"], j["seed"], j["rho"], **j["params"]) for j in JOBS[4:]]
+        while b.info()["active"]:
+            b.step(4)
+        for jid, job in zip(first + late, JOBS):
+            sw, cnt = b.observations(jid, job["params"]["replicas"])
+            want_sw, want_cnt = _alone(job)
+            assert (sw == want_sw).all() and (cnt == want_cnt).all()
+
+
+def test_budget_admission_and_release():
+    p = dict(topo=K.KA_CUBIC, d=3, L=32, m=3, replicas=64)
+    one = K.ka_required_bytes(K.make_params(**p)[0])
+    with K.Batch(hbm_budget=2 * one + one // 2) as b:
+        a = b.add(10, 5, 1, 0.7, **p)
+        b.add(10, 5, 2, 0.7, **p)
+        with pytest.raises(K.KaError) as e:
+            b.add(10, 5, 3, 0.7, **p)
+        assert e.value.status == K.KA_EBUSY
+        used = b.info()["used_bytes"]
+        b.remove(a)
+        assert b.info()["used_bytes"] < used
+        b.add(10, 5, 3, 0.7, **p)
+        while b.info()["active"]:
+            b.step(10)
+
+
+def test_autotune_picks_a_candidate():
+    with K.Batch() as b:
+        for j in JOBS[:6]:
+            b.add(200, 100, j["seed"], j["rho"], **j["params"])
+        k = b.autotune()
+        assert k in (4, 16, 64)
+        while b.info()["active"]:
+            b.step()
