@@ -11,11 +11,15 @@
 //    seed), pair stubs (2q, 2q+1), and reject the whole attempt on a
 //    self-loop or repeated edge.  Pairs are final as soon as the shuffle has
 //    passed them, so a bad attempt is abandoned early; the accepted graph is
-//    the same either way.
+//    the same either way.  Attempts run on several host threads; the graph
+//    kept is always that of the lowest-numbered simple attempt.
 //  * Bond classes of a graph: greedy strong edge colouring of the edges
 //    (u < v, lexicographic ids) in id order; classes in ascending colour.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
+#include <mutex>
+#include <thread>
 
 #include "ka_internal.cuh"
 
@@ -169,52 +173,90 @@ std::string build_cubic_tables(int d, int L, Topology& t) {
   return "";
 }
 
+namespace {
+
+// One attempt of the configuration model.  Returns true, with the rows of
+// the graph in adj, when the pairing is simple.  An attempt gives up early
+// once a lower-numbered attempt has succeeded (`best`), since it can no
+// longer be the one that is kept.
+bool rrg_attempt(int64_t N, int z, const RoundKeys& rk, uint32_t att,
+                 const std::atomic<int64_t>& best, std::vector<uint32_t>& stub,
+                 std::vector<int32_t>& adj, std::vector<uint8_t>& deg) {
+  const int64_t M = N * z;
+  StubRng rng;
+  rng.rk = rk;
+  rng.attempt = att;
+  for (int64_t s = 0; s < M; ++s) stub[s] = (uint32_t)s;
+  std::fill(deg.begin(), deg.end(), 0);
+  for (int64_t k = M - 1; k >= 1; --k) {
+    if ((k & 0xFFFF) == 0 && best.load(std::memory_order_relaxed) < (int64_t)att) return false;
+    const int64_t j = (int64_t)rng.below((uint32_t)k, (uint64_t)(k + 1));
+    std::swap(stub[k], stub[j]);
+    // the pair (k, k+1) for even k, and the pair (0, 1) after step 1, is final
+    int64_t q0;
+    if ((k & 1) == 0)
+      q0 = k;
+    else if (k == 1)
+      q0 = 0;
+    else
+      continue;
+    const int64_t a = stub[q0] / z, b = stub[q0 + 1] / z;
+    if (a == b) return false;
+    for (int s = 0; s < deg[a]; ++s)
+      if (adj[a * z + s] == b) return false;
+    adj[a * z + deg[a]++] = (int32_t)b;
+    adj[b * z + deg[b]++] = (int32_t)a;
+  }
+  return true;
+}
+
+}  // namespace
+
+// The attempts are independent (each has its own counter range), so they run
+// on several host threads; the graph kept is that of the lowest-numbered
+// successful attempt, exactly as in a serial loop over attempts.
 std::string build_rrg(int64_t N, int z, uint64_t graph_seed, Topology& t) {
   if (N < 2 || z < 1 || z > 8 || z >= N || (N * z) % 2 || N * z > 0xFFFFFFFFLL)
     return "random regular graph needs N >= 2, 1 <= z <= 8, z < N, N z even, N z < 2^32";
   const int64_t M = N * z;
-  StubRng rng;
-  rng.rk = round_keys(graph_seed);
-  std::vector<uint32_t> stub(M);
-  std::vector<int32_t> adj((size_t)N * z);
-  std::vector<uint8_t> deg(N);
+  const RoundKeys rk = round_keys(graph_seed);
   const int64_t max_attempts = 1 << 22;
-  for (int64_t att = 0; att < max_attempts; ++att) {
-    rng.attempt = (uint32_t)att;
-    for (int64_t s = 0; s < M; ++s) stub[s] = (uint32_t)s;
-    std::fill(deg.begin(), deg.end(), 0);
-    bool ok = true;
-    for (int64_t k = M - 1; k >= 1; --k) {
-      const int64_t j = (int64_t)rng.below((uint32_t)k, (uint64_t)(k + 1));
-      std::swap(stub[k], stub[j]);
-      // the pair (k, k+1) for even k, and the pair (0, 1) after step 1, is final
-      int64_t q0;
-      if ((k & 1) == 0)
-        q0 = k;
-      else if (k == 1)
-        q0 = 0;
-      else
-        continue;
-      const int64_t a = stub[q0] / z, b = stub[q0 + 1] / z;
-      if (a == b) {
-        ok = false;
-        break;
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nthreads = (int)std::min<int64_t>(std::min<unsigned>(hw, 16u), std::max<int64_t>(1, M >> 15));
+  std::atomic<int64_t> next{0}, best{max_attempts};
+  std::vector<int32_t> result;
+  std::mutex mu;
+  auto worker = [&]() {
+    std::vector<uint32_t> stub(M);
+    std::vector<int32_t> adj((size_t)N * z);
+    std::vector<uint8_t> deg(N);
+    for (;;) {
+      const int64_t att = next.fetch_add(1);
+      if (att >= best.load()) return;
+      if (!rrg_attempt(N, z, rk, (uint32_t)att, best, stub, adj, deg)) continue;
+      std::lock_guard<std::mutex> lock(mu);
+      if (att < best.load()) {
+        best.store(att);
+        result.swap(adj);
+        adj.assign((size_t)N * z, 0);
       }
-      for (int s = 0; s < deg[a]; ++s)
-        if (adj[a * z + s] == b) ok = false;
-      if (!ok) break;
-      adj[a * z + deg[a]++] = (int32_t)b;
-      adj[b * z + deg[b]++] = (int32_t)a;
+      return;
     }
-    if (!ok) continue;
-    for (int64_t v = 0; v < N; ++v) std::sort(adj.begin() + v * z, adj.begin() + (v + 1) * z);
-    t.N = N;
-    t.z = z;
-    t.nbr.swap(adj);
-    t.attempts = (int)std::min<int64_t>(att + 1, 0x7FFFFFFF);
-    return colour_graph(t);
+  };
+  if (nthreads == 1) {
+    worker();
+  } else {
+    std::vector<std::thread> pool;
+    for (int i = 0; i < nthreads; ++i) pool.emplace_back(worker);
+    for (auto& th : pool) th.join();
   }
-  return "random regular graph: no simple graph within the attempt limit";
+  if (best.load() >= max_attempts) return "random regular graph: no simple graph within the attempt limit";
+  for (int64_t v = 0; v < N; ++v) std::sort(result.begin() + v * z, result.begin() + (v + 1) * z);
+  t.N = N;
+  t.z = z;
+  t.nbr.swap(result);
+  t.attempts = (int)std::min<int64_t>(best.load() + 1, 0x7FFFFFFF);
+  return colour_graph(t);
 }
 
 std::string build_graph(int64_t N, int z, const int32_t* nbr, Topology& t) {

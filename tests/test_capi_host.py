@@ -93,7 +93,9 @@ def test_cubic_tables_match_oracle(d, L):
 
 
 @pytest.mark.parametrize("N,z,seed", [(64, 4, 1), (4096, 4, 1), (4096, 4, 7), (1000, 3, 2),
-                                      (500, 6, 3), (33, 2, 5), (64, 5, 4)])
+                                      (500, 6, 3), (33, 2, 5), (64, 5, 4),
+                                      # large enough that attempts run on several threads
+                                      (1 << 15, 4, 1), (30000, 3, 3)])
 def test_rrg_matches_oracle(N, z, seed):
     p, _ = K.make_params(topo=K.KA_RRG, N=N, z=z, m=1, graph_seed=seed)
     t = K.ka_build_topology(p)
