@@ -227,6 +227,23 @@ ka_status ka_batch_create(int32_t device, void *stream, size_t hbm_budget, int32
 ka_status ka_batch_add(ka_batch *b, const ka_params *params, const ka_job_spec *spec,
                        int64_t *job_id);
 
+/* Device bytes a job takes from a batch's budget: its context
+ * (ka_required_bytes) plus its observation buffer of
+ * (sweeps / observe_every + 2) * replicas * 4 int64. */
+ka_status ka_job_bytes(const ka_params *params, const ka_job_spec *spec, size_t *bytes);
+
+/* Admit a job whose context already exists, so that topologies and initial
+ * states can be prepared on other host threads (each with its own stream)
+ * while the batch runs.  ctx must come from ka_create (the batch takes
+ * ownership and frees it on removal), be initialised (ka_init or
+ * ka_set_state) and live on the batch's device.  spec->sweeps is the target
+ * sweep count (absolute, >= the context's sweep); spec->seed and rho are not
+ * used.  The context's stream is synchronised and replaced by the batch's,
+ * and the first observation is recorded at the context's current sweep.
+ * KA_EBUSY when over budget, KA_EINVAL for a context the batch cannot own;
+ * on any error the context stays the caller's. */
+ka_status ka_batch_adopt(ka_batch *b, ka_ctx *ctx, const ka_job_spec *spec, int64_t *job_id);
+
 /* One round: advance every unfinished job by up to max_sweeps sweeps (a job
  * stops early at its next observation point or its target), then record
  * the due observations.  *sweeps_run = the round's length.  Synchronises. */

@@ -79,6 +79,8 @@ _SIGS = {
                                     C.c_void_p, C.c_void_p]),
     "ka_batch_create": (C.c_int, [C.c_int32, C.c_void_p, C.c_size_t, C.c_int32, _P(C.c_void_p)]),
     "ka_batch_add": (C.c_int, [C.c_void_p, _P(ka_params), _P(ka_job_spec), _P(C.c_int64)]),
+    "ka_job_bytes": (C.c_int, [_P(ka_params), _P(ka_job_spec), _P(C.c_size_t)]),
+    "ka_batch_adopt": (C.c_int, [C.c_void_p, C.c_void_p, _P(ka_job_spec), _P(C.c_int64)]),
     "ka_batch_step": (C.c_int, [C.c_void_p, C.c_int64, _P(C.c_int64)]),
     "ka_batch_autotune": (C.c_int, [C.c_void_p, _P(C.c_int64)]),
     "ka_batch_poll": (C.c_int, [C.c_void_p, C.c_int64, _P(C.c_int64), _P(C.c_int32)]),
@@ -124,7 +126,7 @@ class Ctx:
 
     def __init__(self, handle: int, keep=()):
         self.handle = C.c_void_p(handle)
-        self._keep = list(keep)
+        self._keep = keep  # any objects the context must not outlive
         self.info = None
 
     def __bool__(self):
@@ -156,6 +158,14 @@ def make_params(topo: int = KA_CUBIC, d: int = 3, L: int = 16, z: int = 0, N: in
 def ka_required_bytes(params: ka_params) -> int:
     out = C.c_size_t(0)
     _check(load().ka_required_bytes(C.byref(params), C.byref(out)), "ka_required_bytes")
+    return out.value
+
+
+def ka_job_bytes(params: ka_params, sweeps: int, observe_every: int) -> int:
+    """Device bytes a job takes from a batch's budget (context + observations)."""
+    out = C.c_size_t(0)
+    spec = ka_job_spec(sweeps, observe_every, 0, 0.0)
+    _check(load().ka_job_bytes(C.byref(params), C.byref(spec), C.byref(out)), "ka_job_bytes")
     return out.value
 
 
@@ -299,6 +309,17 @@ class Batch:
         jid = C.c_int64(0)
         _check(load().ka_batch_add(self.handle, C.byref(p), C.byref(spec), C.byref(jid)),
                "ka_batch_add")
+        return jid.value
+
+    def adopt(self, ctx: Ctx, sweeps: int, observe_every: int) -> int:
+        """Admit an initialised context made by ka_create; the batch takes it over.
+
+        Raises KaError(KA_EBUSY) when over budget (the context stays the caller's)."""
+        spec = ka_job_spec(sweeps, observe_every, 0, 0.0)
+        jid = C.c_int64(0)
+        _check(load().ka_batch_adopt(self.handle, ctx.handle, C.byref(spec), C.byref(jid)),
+               "ka_batch_adopt")
+        ctx.handle = C.c_void_p(0)
         return jid.value
 
     def step(self, max_sweeps: int = 0) -> int:

@@ -361,6 +361,60 @@ ka_status run_round(ka_batch* b, int64_t k_req, int64_t* ran) {
   return KA_OK;
 }
 
+size_t obs_bytes(const ka_job_spec* spec, int64_t replicas) {
+  const int64_t cap = spec->sweeps / spec->observe_every + 2;
+  return (size_t)cap * (size_t)replicas * 4 * sizeof(int64_t);
+}
+
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev)
+      cudaSetDevice(dev);
+    else
+      prev = -1;
+  }
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// Make an initialised context (owning its buffer) a job of the batch: move
+// it onto the batch's stream, allocate its observation buffer and record
+// the first observation.  On failure the context is left to the caller.
+ka_status enrol(ka_batch* b, ka_ctx* ctx, const ka_job_spec* spec, int64_t* job_id) {
+  const size_t ob = obs_bytes(spec, ctx->R);
+  Job* j = new Job();
+  if (cudaMalloc((void**)&j->obs_dev, ob) != cudaSuccess) {
+    cudaGetLastError();
+    delete j;
+    return KA_ENOMEM;
+  }
+  ctx->stream = b->stream;
+  ctx->prm.stream = b->stream;
+  j->ctx = ctx;
+  j->buf = ctx->buf;
+  j->t = ctx->sweep;
+  j->target = spec->sweeps;
+  j->every = spec->observe_every;
+  j->cap = spec->sweeps / spec->observe_every + 2;
+  j->batched = !(ctx->topo == KA_CUBIC && !ctx->pencil);
+  const ka_status st = observe_job(b, j);
+  if (st) {
+    cudaFree(j->obs_dev);
+    delete j;
+    return st;
+  }
+  j->id = b->next_id++;
+  j->bytes = ctx->bytes + ob;
+  if (j->t >= j->target) j->finished = true;
+  b->jobs[j->id] = j;
+  b->used += j->bytes;
+  b->dirty = true;
+  if (job_id) *job_id = j->id;
+  return KA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -390,6 +444,15 @@ ka_status ka_batch_create(int32_t device, void* stream, size_t hbm_budget, int32
   return KA_OK;
 }
 
+ka_status ka_job_bytes(const ka_params* params, const ka_job_spec* spec, size_t* bytes) {
+  if (!params || !spec || !bytes || spec->sweeps < 0 || spec->observe_every < 1) return KA_EINVAL;
+  size_t ctx_bytes = 0;
+  const ka_status st = ka::context_bytes(params, &ctx_bytes);
+  if (st) return st;
+  *bytes = ctx_bytes + obs_bytes(spec, params->replicas);
+  return KA_OK;
+}
+
 ka_status ka_batch_add(ka_batch* b, const ka_params* params, const ka_job_spec* spec,
                        int64_t* job_id) {
   if (!b || !params || !spec || spec->sweeps < 0 || spec->observe_every < 1) return KA_EINVAL;
@@ -400,49 +463,35 @@ ka_status ka_batch_add(ka_batch* b, const ka_params* params, const ka_job_spec* 
   size_t bytes = 0;
   ka_status st = ka::context_bytes(&prm, &bytes);
   if (st) return st;
-  const int64_t cap = spec->sweeps / spec->observe_every + 2;
-  const size_t obs_bytes = (size_t)cap * prm.replicas * 4 * sizeof(int64_t);
-  const size_t need = bytes + obs_bytes;
-  if (b->used + need > b->budget) return KA_EBUSY;
-  int prev = -1;
-  cudaGetDevice(&prev);
-  cudaSetDevice(b->device);
-  Job* j = new Job();
-  cudaError_t e = cudaMalloc(&j->buf, bytes);
-  if (!e) e = cudaMalloc((void**)&j->obs_dev, obs_bytes);
-  if (e) {
+  if (b->used + bytes + obs_bytes(spec, prm.replicas) > b->budget) return KA_EBUSY;
+  DeviceScope scope(b->device);
+  void* buf = nullptr;
+  if (cudaMalloc(&buf, bytes) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(j->buf);
-    delete j;
-    if (prev >= 0) cudaSetDevice(prev);
     return KA_ENOMEM;
   }
-  st = ka::create_context(&prm, j->buf, bytes, true, &j->ctx);
-  if (!st) st = ka_init(j->ctx, spec->seed, spec->rho);
+  ka_ctx* ctx = nullptr;
+  st = ka::create_context(&prm, buf, bytes, true, &ctx);
   if (st) {
-    if (j->ctx)
-      ka_destroy(j->ctx);
-    else
-      cudaFree(j->buf);
-    cudaFree(j->obs_dev);
-    delete j;
-    if (prev >= 0) cudaSetDevice(prev);
+    cudaFree(buf);
     return st;
   }
-  j->id = b->next_id++;
-  j->bytes = need;
-  j->target = spec->sweeps;
-  j->every = spec->observe_every;
-  j->cap = cap;
-  j->batched = !(j->ctx->topo == KA_CUBIC && !j->ctx->pencil);
-  st = observe_job(b, j);  // sweep 0
-  if (j->target == 0) j->finished = true;
-  b->jobs[j->id] = j;
-  b->used += need;
-  b->dirty = true;
-  if (prev >= 0) cudaSetDevice(prev);
-  if (job_id) *job_id = j->id;
+  st = ka_init(ctx, spec->seed, spec->rho);
+  if (!st) st = enrol(b, ctx, spec, job_id);
+  if (st) ka_destroy(ctx);
   return st;
+}
+
+ka_status ka_batch_adopt(ka_batch* b, ka_ctx* ctx, const ka_job_spec* spec, int64_t* job_id) {
+  if (!b || !ctx || !spec || spec->observe_every < 1) return KA_EINVAL;
+  if (spec->sweeps < ctx->sweep || spec->sweeps >= ((int64_t)1 << 32)) return KA_EINVAL;
+  if (!ctx->owns || ctx->device != b->device) return KA_EINVAL;
+  if (!ctx->initialized) return KA_ESTATE;
+  if (b->used + ctx->bytes + obs_bytes(spec, ctx->R) > b->budget) return KA_EBUSY;
+  DeviceScope scope(b->device);
+  const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e) return cuda_err(b, e, "adopted context");
+  return enrol(b, ctx, spec, job_id);
 }
 
 ka_status ka_batch_step(ka_batch* b, int64_t max_sweeps, int64_t* sweeps_run) {

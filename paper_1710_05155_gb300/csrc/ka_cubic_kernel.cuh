@@ -43,6 +43,8 @@
 // (ka_cubic_d*.cu), one per (d, batched), so that they build in parallel.
 #pragma once
 
+#include <mutex>
+
 #include "ka_internal.cuh"
 
 namespace ka {
@@ -555,35 +557,59 @@ __global__ void __launch_bounds__(kThreads, KA_CUBIC_MIN_BLOCKS)
   }
 }
 
+// Per kernel instance and device: the dynamic shared memory granted so far
+// and the resident CTAs per SM at the last shared-memory size.  Guarded, as
+// contexts may be created and swept from several host threads.
+struct LaunchCache {
+  static constexpr int kDevices = 16;
+  std::mutex mu;
+  size_t granted[kDevices] = {}, occ_smem[kDevices] = {};
+  int per_sm[kDevices] = {}, sms[kDevices] = {};
+};
+
+// Launch a persistent grid: at most as many CTAs as fit on the device at once.
+template <typename Kern>
+cudaError_t launch_persistent(Kern kern, LaunchCache& lc, const GroupArgs& a, const BatchArgs& ba,
+                              unsigned blocks, size_t smem, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= LaunchCache::kDevices) return cudaErrorInvalidDevice;
+  unsigned cap;
+  {
+    std::lock_guard<std::mutex> lock(lc.mu);
+    if (smem > lc.granted[dev]) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      lc.granted[dev] = smem;
+    }
+    if (lc.per_sm[dev] == 0 || lc.occ_smem[dev] != smem) {
+      int per_sm = 0, sms = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+      lc.per_sm[dev] = per_sm < 1 ? 1 : per_sm;
+      lc.sms[dev] = sms < 1 ? 1 : sms;
+      lc.occ_smem[dev] = smem;
+    }
+    cap = (unsigned)(lc.per_sm[dev] * lc.sms[dev]);
+  }
+  kern<<<blocks < cap ? blocks : cap, kThreads, smem, st>>>(a, ba);
+  return cudaGetLastError();
+}
+
 template <int D, int V, bool X, bool B>
 cudaError_t launch_dx(const GroupArgs& a, const BatchArgs& ba, int m, unsigned blocks, size_t smem,
                       cudaStream_t st) {
   constexpr int Z = 2 * D;
   const int mm = m < Z - 1 ? m : Z - 1;
   switch (mm) {
-#define KA_CASE(MM)                                                                         \
-  case MM:                                                                                  \
-    if constexpr (MM <= Z - 1) {                                                            \
-      auto kern = k_cubic_group<D, V, MM, X, B>;                                               \
-      static size_t granted = 0;                                                            \
-      if (smem > granted) {                                                                 \
-        cudaError_t e = cudaFuncSetAttribute(                                               \
-            kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                  \
-        if (e != cudaSuccess) return e;                                                     \
-        granted = smem;                                                                     \
-      }                                                                                     \
-      static int per_sm = 0, sms = 0;                                                       \
-      if (per_sm == 0) {                                                                    \
-        int dev = 0;                                                                        \
-        cudaGetDevice(&dev);                                                                \
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);                  \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);       \
-        if (per_sm < 1) per_sm = 1;                                                         \
-      }                                                                                     \
-      const unsigned grid = blocks < (unsigned)(per_sm * sms) ? blocks : (unsigned)(per_sm * sms); \
-      kern<<<grid, kThreads, smem, st>>>(a, ba);                                            \
-      return cudaGetLastError();                                                            \
-    }                                                                                       \
+#define KA_CASE(MM)                                                                    \
+  case MM:                                                                             \
+    if constexpr (MM <= Z - 1) {                                                       \
+      static LaunchCache lc;                                                           \
+      return launch_persistent(k_cubic_group<D, V, MM, X, B>, lc, a, ba, blocks, smem, \
+                               st);                                                    \
+    }                                                                                  \
     break;
     KA_CASE(0)
     KA_CASE(1)

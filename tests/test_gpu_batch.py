@@ -108,3 +108,32 @@ def test_autotune_picks_a_candidate():
         assert k in (4, 16, 64)
         while b.info()["active"]:
             b.step()
+
+
+def test_adopt_rules():
+    p = dict(topo=K.KA_CUBIC, d=3, L=16, m=3, replicas=64)
+    with K.Batch() as b:
+        params, keep = K.make_params(**p)
+        fresh = K.ka_create(params, keep)
+        with pytest.raises(K.KaError) as e:  # not initialised
+            b.adopt(fresh, 10, 5)
+        assert e.value.status == K.KA_ESTATE
+        K.ka_init(fresh, 3, 0.7)
+        K.ka_sweep(fresh, 4)  # adopted mid-run: observations continue from sweep 4
+        jid = b.adopt(fresh, 12, 5)
+        assert not fresh  # the batch owns it now
+        sim = K.Simulation(**p)  # caller-owned buffer: cannot be handed over
+        sim.init(3, 0.7)
+        with pytest.raises(K.KaError) as e:
+            b.adopt(sim.ctx, 10, 5)
+        assert e.value.status == K.KA_EINVAL
+        while b.info()["active"]:
+            b.step(3)
+        sw, cnt = b.observations(jid, 64)
+        assert list(sw) == [4, 5, 10, 12]
+        for t, c in zip(sw, cnt):
+            if t == 4:
+                continue
+            sim.sweep(int(t) - sim.observe()[0])
+            assert (sim.observe()[1] == c).all()
+        sim.close()
