@@ -14,6 +14,11 @@ Metric: attempted KA moves per second counted per site x replica
 
 --impl reference times the CPU oracle (the serial restatement of the paper
 used by the tests) on a bounded sample of the same workload.
+
+Two more workloads, each printing its own JSON line (one GPU):
+
+  python bench.py --workload batched   # 512-instance mix: batched rounds vs per-job launches
+  python bench.py --workload served    # Poisson request trace through the serving loop
 """
 from __future__ import annotations
 
@@ -112,7 +117,7 @@ def measured_traffic():
     import hashlib
 
     prof = os.path.join(ROOT, "profiles", "k_cubic_group_L128_R256.md")
-    src = os.path.join(ROOT, "paper_1710_05155_gb300", "csrc", "ka_sweep_cubic.cu")
+    src = os.path.join(ROOT, "paper_1710_05155_gb300", "csrc", "ka_cubic_kernel.cuh")
     try:
         fields = {}
         for line in open(prof):
@@ -168,6 +173,23 @@ def run_reference(args, rank: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x: float, dist=None, device: str = "cpu") -> float:
+    """The largest x over all ranks (x itself on one process): the job's time
+    is its slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(rank: int) -> int:
+    """Dynamics seed of a rank: every rank simulates its own replicas (weak scaling)."""
+    return SEED + 1000 * rank
+
+
 def run_native(args, rank: int, world: int) -> None:
     import torch
 
@@ -187,7 +209,7 @@ def run_native(args, rank: int, world: int) -> None:
     sims = []
     for k, rho in enumerate(RHOS):
         sim = K.Simulation(topo=K.KA_CUBIC, d=D, L=L, m=M, replicas=R, device=dev, stream=stream)
-        sim.init(SEED + 1000 * rank, rho)
+        sim.init(rank_seed(rank), rho)
         sims.append(sim)
     counts_dev = [torch.zeros((R, 4), dtype=torch.int64, device=f"cuda:{dev}") for _ in sims]
     P = sims[0].info["planes"]
@@ -218,9 +240,7 @@ def run_native(args, rank: int, world: int) -> None:
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     if dist:
-        t = torch.tensor([ms], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, f"cuda:{dev}")
         dist.barrier()
     moves = N_SITES * R * S * len(sims) * args.steps * world
     value = moves / (ms / 1000.0)
@@ -266,9 +286,7 @@ def run_native(args, rank: int, world: int) -> None:
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
     if dist:
-        t = torch.tensor([e2e_s], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, dist, f"cuda:{dev}")
     e2e_value = N_SITES * R * S * len(sims) * e2e_steps * world / e2e_s
     h2d = len(sims) * 3 * WORDS * N_SITES * 8
     d2h = len(sims) * R * 4 * 8
@@ -306,6 +324,107 @@ def run_native(args, rank: int, world: int) -> None:
         dist.destroy_process_group()
 
 
+def _run_batch(jobs, flags, dev, k):
+    """Run every job to its target in one batch; returns (device ms, rounds, round length)."""
+    import torch
+
+    import paper_1710_05155_gb300 as K
+
+    stream = torch.cuda.Stream(device=dev)
+    b = K.Batch(device=dev, stream=stream.cuda_stream, flags=flags)
+    for j in jobs:
+        b.add(j.sweeps, j.every, j.seed, j.rho, **j.params)
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    rounds = 0
+    if k == 0 and not (flags & K.KA_BATCH_PLAIN):
+        k = b.autotune()  # times real rounds of this batch: part of the timed work
+        rounds += 3
+    while b.info()["active"]:
+        b.step(k or 16)
+        rounds += 1
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    b.close()
+    return ms, rounds, k
+
+
+def run_batched(args) -> None:
+    """Instance mix: the same jobs batched (graph-captured rounds) and with
+    per-job launches (one ka_sweep loop per instance on one stream)."""
+    import torch
+
+    import paper_1710_05155_gb300 as K
+    from paper_1710_05155_gb300 import workloads
+
+    dev = 0
+    torch.cuda.set_device(dev)
+    jobs = workloads.instance_mix(args.jobs, master=1)
+    jobs = [workloads.Job(j.params, max(1, round(j.sweeps * args.sweep_scale)), j.every, j.seed,
+                          j.rho) for j in jobs]
+    moves = float(sum(j.work for j in jobs))
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ms_b, rounds, k = _run_batch(jobs, K.KA_BATCH_GRAPH, dev, args.round)
+    ms_p, _, _ = _run_batch(jobs, K.KA_BATCH_PLAIN, dev, k)
+    clk = clocks.stop()
+    value = moves / (ms_b / 1000.0)
+    line = {
+        "metric": METRIC + ", batched vs plain", "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": 1, "warmup": 0, "ms_per_step": ms_b, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"{args.jobs} instances: cubic d=3 m=3 L in {{16..96}} or RRG "
+                               f"z=4 m=2 N=2^12..2^18, R=64, rho U[0.75,0.88], sweeps "
+                               f"U[1000,20000] x {args.sweep_scale}, observe every 100",
+                   "round_sweeps": k, "rounds": rounds, "site_replica_moves": moves},
+        "plain": {"value": moves / (ms_p / 1000.0), "unit": UNIT, "ms": ms_p},
+        "batched_over_plain": ms_p / ms_b,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_served(args) -> None:
+    """Request trace through the serving loop, then again at a fraction of the
+    capacity the first run measured."""
+    import paper_1710_05155_gb300.serve as S
+    from paper_1710_05155_gb300 import workloads
+
+    budget = int(150 * (1 << 30))
+
+    def serve(rate):
+        jobs = workloads.scaled(workloads.request_trace(args.jobs, rate, 1), args.sweep_scale)
+        be = S.DeviceBackend(0, budget, True, 4)
+        try:
+            rep = S.Server(be, round_sweeps=args.round).run(jobs)
+        finally:
+            be.close()
+        rep["rate_per_s"] = rate
+        rep["mean_job_moves"] = float(np.mean([j.work for j in jobs]))
+        return rep
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    first = serve(200.0)
+    capacity = first["moves_per_s"] / first["mean_job_moves"]
+    second = serve(0.7 * capacity)
+    clk = clocks.stop()
+    line = {
+        "metric": METRIC + ", served", "value": first["moves_per_s"], "unit": UNIT, "n_gpus": 1,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.jobs} Poisson requests at 200/s: cubic L in 4*[8..32] or "
+                               f"RRG z=4 N=2^14..2^20, m in {{2,3}}, R in {{64..256}}, "
+                               f"sweeps log-U[1e3,1e5] x {args.sweep_scale}, 150 GB budget"},
+        "offered_200_per_s": first,
+        "at_0.7_capacity": {"capacity_jobs_per_s": capacity, **second},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -314,10 +433,24 @@ def main():
     ap.add_argument("--sweeps", type=int, default=100, help="sweeps per context per step")
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["cubic", "batched", "served"], default="cubic")
+    ap.add_argument("--jobs", type=int, default=0, help="instances (batched: 512, served: 100)")
+    ap.add_argument("--sweep-scale", type=float, default=0.05,
+                    help="batched/served: fraction of each job's sweeps that is run")
+    ap.add_argument("--round", type=int, default=0, help="batched/served: sweeps per round "
+                                                         "(0: autotuned)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    if args.impl == "reference":
+    if args.workload != "cubic":
+        if args.impl == "reference" or world > 1:
+            if rank == 0:
+                print(json.dumps({"impl": args.impl, "unavailable":
+                                  "the batched and served workloads run on one GPU, natively"}))
+            return
+        args.jobs = args.jobs or (512 if args.workload == "batched" else 100)
+        (run_batched if args.workload == "batched" else run_served)(args)
+    elif args.impl == "reference":
         run_reference(args, rank)
     else:
         run_native(args, rank, world)
