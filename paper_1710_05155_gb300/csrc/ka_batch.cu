@@ -40,6 +40,7 @@ struct CubicClass {
   std::vector<ka::CubicUnit> units;
   std::vector<Job*> owner;
   ka::CubicUnit* dev = nullptr;
+  uint32_t* tile_unit_dev[2] = {nullptr, nullptr};  // unit of every global tile, per kind
   uint32_t ntiles[2] = {0, 0};
   int PSmax = 0;
 };
@@ -179,6 +180,20 @@ cudaError_t rebuild(ka_batch* b) {
   cudaError_t e = cudaSuccess;
   for (auto& cc : b->cubic) {
     if ((e = dev_alloc(b, &cc.dev, cc.units.size()))) return e;
+    for (int mode = 0; mode < 2; ++mode) {
+      std::vector<uint32_t> owner(cc.ntiles[mode]);
+      for (size_t u = 0; u < cc.units.size(); ++u) {
+        const uint32_t end = (u + 1 < cc.units.size()) ? cc.units[u + 1].tile0[mode] : cc.ntiles[mode];
+        for (uint32_t g = cc.units[u].tile0[mode]; g < end; ++g) owner[g] = (uint32_t)u;
+      }
+      if ((e = dev_alloc(b, &cc.tile_unit_dev[mode], owner.size()))) return e;
+      if (!owner.empty() &&
+          (e = cudaMemcpyAsync(cc.tile_unit_dev[mode], owner.data(), owner.size() * sizeof(uint32_t),
+                               cudaMemcpyHostToDevice, b->stream)))
+        return e;
+      // the host vector must outlive the copy
+      if ((e = cudaStreamSynchronize(b->stream))) return e;
+    }
   }
   for (auto& gc : b->graph) {
     const int n = (int)gc.units.size();
@@ -231,7 +246,8 @@ cudaError_t issue_round(ka_batch* b, int64_t k) {
       for (int mu = 0; mu < cc.d && !e; ++mu)
         for (int par = 0; par < npar && !e; ++par) {
           const bool x = (mu == 0) || cc.d == 1;
-          e = ka::launch_cubic_group_batch(cc.dev, (int)cc.units.size(), cc.ntiles[x ? 0 : 1],
+          e = ka::launch_cubic_group_batch(cc.dev, cc.tile_unit_dev[x ? 0 : 1],
+                                           (int)cc.units.size(), cc.ntiles[x ? 0 : 1],
                                            cc.PSmax, cc.d, cc.V, cc.m, mu, par, (uint32_t)s,
                                            b->stream);
         }

@@ -317,13 +317,9 @@ __device__ void unit_args(const CubicUnit& u, const BatchArgs& ba, GroupArgs& a)
 template <int V, bool X>
 __device__ void resolve(const BatchArgs& ba, uint32_t g, GroupArgs& a, uint32_t& local) {
   const int mode = X ? 0 : 1;
-  int lo = 0, hi = ba.nunits - 1;  // last unit whose first tile is <= g
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (ba.units[mid].tile0[mode] <= g) lo = mid; else hi = mid - 1;
-  }
-  unit_args<V>(ba.units[lo], ba, a);
-  local = g - ba.units[lo].tile0[mode];
+  const uint32_t u = ba.tile_unit[g];
+  unit_args<V>(ba.units[u], ba, a);
+  local = g - ba.units[u].tile0[mode];
   if (local >= a.ntiles) a.ntiles = 0;  // finished unit: no work in this tile
 }
 

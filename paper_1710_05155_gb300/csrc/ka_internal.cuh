@@ -113,6 +113,7 @@ struct CubicUnit {
 // Launch-wide arguments of a batched group launch.
 struct BatchArgs {
   CubicUnit* units;
+  const uint32_t* tile_unit;  // the unit owning each global tile of this launch
   int nunits;
   int mu, par;
   uint32_t ntiles;  // all tiles of all units for this mu
@@ -121,8 +122,10 @@ struct BatchArgs {
 };
 
 // Group (mu, par) of sweep t_base + sweep_offset for every unit of a batch
-// (all units share d, V and m); ntiles = sum of the units' tiles for this mu.
-cudaError_t launch_cubic_group_batch(CubicUnit* units_dev, int nunits, uint32_t ntiles, int PSmax,
+// (all units share d, V and m); ntiles = sum of the units' tiles for this mu,
+// tile_unit[g] = the unit owning global tile g.
+cudaError_t launch_cubic_group_batch(CubicUnit* units_dev, const uint32_t* tile_unit, int nunits,
+                                     uint32_t ntiles, int PSmax,
                                      int d, int V, int m, int mu, int par, uint32_t sweep_offset,
                                      cudaStream_t st);
 

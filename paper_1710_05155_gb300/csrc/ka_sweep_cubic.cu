@@ -69,7 +69,8 @@ cudaError_t launch_cubic_group(const Planes& pl, int q, const CubicShape& s, int
   return dispatch<false>(d, V, x, a, none, s.m, blocks, smem, st);
 }
 
-cudaError_t launch_cubic_group_batch(CubicUnit* units_dev, int nunits, uint32_t ntiles, int PSmax,
+cudaError_t launch_cubic_group_batch(CubicUnit* units_dev, const uint32_t* tile_unit, int nunits,
+                                     uint32_t ntiles, int PSmax,
                                      int d, int V, int m, int mu, int par, uint32_t sweep_offset,
                                      cudaStream_t st) {
   if (nunits <= 0 || ntiles == 0) return cudaSuccess;
@@ -77,6 +78,7 @@ cudaError_t launch_cubic_group_batch(CubicUnit* units_dev, int nunits, uint32_t 
     return cudaErrorInvalidValue;
   BatchArgs ba;
   ba.units = units_dev;
+  ba.tile_unit = tile_unit;
   ba.nunits = nunits;
   ba.mu = mu;
   ba.par = par;
