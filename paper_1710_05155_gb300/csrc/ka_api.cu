@@ -65,9 +65,10 @@ const char* check_params(const ka_params* p, Shape& s) {
     return "unknown topology";
   }
   if (s.m < 0 || s.m > s.z - 1) return "m must be in [0, z-1]";
-  // words per site and plane: the pencil kernel reads a whole 32-byte sector
-  // per site when 4 words fit; the edge-gather kernel pairs at most 2
-  if (s.pencil && s.W % 4 == 0) s.V = 4;
+  // words per site and plane: a whole 32-byte sector per site when 4 words
+  // fit (the pencil kernel stages sectors; the edge-gather kernel's random
+  // accesses move whole sectors anyway)
+  if (s.W % 4 == 0) s.V = 4;
   s.P = s.W / s.V;
   return nullptr;
 }

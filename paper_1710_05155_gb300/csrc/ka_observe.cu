@@ -8,9 +8,10 @@
 //   persist_occ = sum_i n0_i & p_i
 //   persist_all = sum_i p_i
 //
-// Each thread adds up to 255 words into bit-sliced counters (8 slices: one
+// Each thread adds up to 63 words into bit-sliced counters (6 slices: one
 // uint64 per binary digit, so all 64 replicas count in parallel with a
-// ripple adder).  Lanes holding the same word position are then summed in
+// ripple adder); the words per thread are chosen so that the grid fills the
+// device, four independent loads in flight per thread.  Lanes holding the same word position are then summed in
 // bit-sliced form through warp shuffles, the warp total is turned into one
 // integer per replica, and blocks accumulate in shared memory before one
 // 64-bit atomic per counter goes to global memory.
@@ -19,8 +20,8 @@
 namespace ka {
 namespace {
 
-constexpr int kSlices = 8;        // per-thread counters hold up to 255
-constexpr int kPerThread = 255;   // words per thread
+constexpr int kSlices = 6;        // per-thread counters hold up to 63
+constexpr int kPerThread = 63;    // most words per thread
 constexpr int kWide = kSlices + 5;  // after summing 32 lanes
 
 __device__ __forceinline__ void ripple_add(uint64_t (&c)[kSlices], uint64_t x) {
@@ -45,7 +46,8 @@ __device__ __forceinline__ void shfl_add(uint64_t (&c)[kWide], int off) {
 }
 
 template <int V>
-__global__ void __launch_bounds__(256) k_observe(Planes pl, unsigned long long* counts) {
+__global__ void __launch_bounds__(256, 2) k_observe(Planes pl, unsigned long long* counts,
+                                                 int per_thread) {
   __shared__ unsigned int acc[4][64 * V];
   const int q = blockIdx.y;
   for (int k = threadIdx.x; k < 4 * 64 * V; k += blockDim.x) (&acc[0][0])[k] = 0;
@@ -55,20 +57,29 @@ __global__ void __launch_bounds__(256) k_observe(Planes pl, unsigned long long* 
   const size_t base = (size_t)q * E;
   // element e of the plane holds word h = e % V of site e / V; blockDim and
   // the stride are even, so a thread always sees the same h
-  const size_t e0 = (size_t)blockIdx.x * blockDim.x * kPerThread + threadIdx.x;
+  const size_t e0 = (size_t)blockIdx.x * blockDim.x * per_thread + threadIdx.x;
   uint64_t c[4][kSlices];
 #pragma unroll
   for (int o = 0; o < 4; ++o)
 #pragma unroll
     for (int s = 0; s < kSlices; ++s) c[o][s] = 0;
-  for (int k = 0; k < kPerThread; ++k) {
-    const size_t e = e0 + (size_t)k * blockDim.x;
-    if (e >= E) break;
-    const uint64_t n = pl.n[base + e], n0 = pl.n0[base + e], p = pl.p[base + e];
-    ripple_add(c[0], n);
-    ripple_add(c[1], n & n0);
-    ripple_add(c[2], n0 & p);
-    ripple_add(c[3], p);
+  for (int k = 0; k < per_thread; k += 4) {
+    uint64_t n[4], n0[4], p[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const size_t e = e0 + (size_t)(k + u) * blockDim.x;
+      const bool in = (k + u < per_thread) && e < E;
+      n[u] = in ? pl.n[base + e] : 0ull;
+      n0[u] = in ? pl.n0[base + e] : 0ull;
+      p[u] = in ? pl.p[base + e] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      ripple_add(c[0], n[u]);
+      ripple_add(c[1], n[u] & n0[u]);
+      ripple_add(c[2], n0[u] & p[u]);
+      ripple_add(c[3], p[u]);
+    }
   }
 
   const int lane = threadIdx.x & 31;
@@ -114,14 +125,21 @@ cudaError_t launch_observe(const Planes& pl, int R, unsigned long long* counts_d
                            cudaStream_t st) {
   cudaError_t err = cudaMemsetAsync(counts_dev, 0, (size_t)R * 4 * sizeof(unsigned long long), st);
   if (err != cudaSuccess) return err;
-  const size_t per_block = (size_t)256 * kPerThread;
-  dim3 grid((unsigned)((pl.plane_elems() + per_block - 1) / per_block), (unsigned)pl.P);
+  // words per thread: enough blocks for four per SM, at most kPerThread
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t E = pl.plane_elems();
+  const size_t want = (size_t)256 * 4 * (size_t)(sms > 0 ? sms : 148);
+  int per_thread = (int)((E + want - 1) / want);
+  per_thread = per_thread < 4 ? 4 : (per_thread > kPerThread ? kPerThread : per_thread);
+  const size_t per_block = (size_t)256 * per_thread;
+  dim3 grid((unsigned)((E + per_block - 1) / per_block), (unsigned)pl.P);
   if (pl.V == 4)
-    k_observe<4><<<grid, 256, 0, st>>>(pl, counts_dev);
+    k_observe<4><<<grid, 256, 0, st>>>(pl, counts_dev, per_thread);
   else if (pl.V == 2)
-    k_observe<2><<<grid, 256, 0, st>>>(pl, counts_dev);
+    k_observe<2><<<grid, 256, 0, st>>>(pl, counts_dev, per_thread);
   else
-    k_observe<1><<<grid, 256, 0, st>>>(pl, counts_dev);
+    k_observe<1><<<grid, 256, 0, st>>>(pl, counts_dev, per_thread);
   return cudaGetLastError();
 }
 

@@ -1,11 +1,23 @@
 // ka_sweep_graph.cu -- edge-gather sweep kernel for one bond class.
 //
 // One thread per (bond of the class, plane).  The bond (u, v) gathers the
-// words of u, v and of their neighbours from the int32 neighbour list, counts
-// the occupied neighbours of u other than v and of v other than u with
-// bit-sliced adders (64 replicas per word), and applies the exchange rule of
-// section 2.1 (rules (a)-(c)) under the replica's Philox gate bit.  Bonds of
-// a class form a strong matching, so threads never touch each other's sites.
+// words of u, v and of their other neighbours from the int32 neighbour
+// list, counts the occupied neighbours of u other than v and of v other
+// than u with bit-sliced adders (64 replicas per word), and applies the
+// exchange rule of section 2.1 (rules (a)-(c)) under the replica's Philox
+// gate bit.  Bonds of a class form a strong matching, so threads never
+// touch each other's sites.
+//
+// A plane holds V = 1, 2 or 4 words per site, so a site's words share one
+// 32-byte sector: every gather is a random access, and the sector is the
+// unit the memory system moves.  The partner's word is not gathered twice.
+//
+// Classes run as consecutive launches with programmatic dependent launch:
+// a class launch may start while the previous one drains, and does all the
+// work that reads only static tables (its bond, the two neighbour rows, the
+// gate words) before it waits for the previous class to complete.
+#include <utility>
+
 #include "ka_internal.cuh"
 
 namespace ka {
@@ -49,85 +61,103 @@ __device__ __forceinline__ uint64_t le3(uint64_t b2, uint64_t b1, uint64_t b0) {
   }
 }
 
+// the V words of site i (16-byte vectors for V >= 2; a site's words are
+// 8 V-byte aligned)
 template <int V>
 __device__ __forceinline__ void ld(const uint64_t* base, int64_t i, uint64_t (&o)[V]) {
-  if constexpr (V == 2) {
-    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(base + 2 * i);
-    o[0] = v.x;
-    o[1] = v.y;
-  } else {
+  if constexpr (V == 1) {
     o[0] = base[i];
+  } else {
+#pragma unroll
+    for (int h = 0; h < V; h += 2) {
+      const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(base + V * i + h);
+      o[h] = v.x;
+      o[h + 1] = v.y;
+    }
   }
 }
 
 template <int V>
 __device__ __forceinline__ void st(uint64_t* base, int64_t i, const uint64_t (&o)[V]) {
-  if constexpr (V == 2) {
-    *reinterpret_cast<ulonglong2*>(base + 2 * i) = make_ulonglong2(o[0], o[1]);
-  } else {
+  if constexpr (V == 1) {
     base[i] = o[0];
+  } else {
+#pragma unroll
+    for (int h = 0; h < V; h += 2)
+      *reinterpret_cast<ulonglong2*>(base + V * i + h) = make_ulonglong2(o[h], o[h + 1]);
   }
 }
 
-template <int V, int M>
-__global__ void __launch_bounds__(256) k_graph_class(const ClassArgs a) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.count) return;
-  const int q = blockIdx.y;
-  uint64_t* np = a.n + (size_t)q * a.plane_elems;
-  uint64_t* pp = a.p + (size_t)q * a.plane_elems;
-  const int32_t u = a.bu[e], v = a.bv[e];
-  const uint32_t id = a.bid[e];
-  const int z = a.z;
+// programmatic dependent launch: let the next class launch start, and wait
+// for the previous one before touching the state
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 
+constexpr int kMaxZ = 8;
+
+// neighbour row of x (z <= 8); z = 4 rows are one 16-byte load
+__device__ __forceinline__ void load_row(const int32_t* nbr, int z, int32_t x,
+                                         int32_t (&r)[kMaxZ]) {
+  if (z == 4) {
+    const int4 q = *reinterpret_cast<const int4*>(nbr + (int64_t)x * 4);
+    r[0] = q.x;
+    r[1] = q.y;
+    r[2] = q.z;
+    r[3] = q.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < kMaxZ; ++k)
+      if (k < z) r[k] = nbr[(int64_t)x * z + k];
+  }
+}
+
+// Graph gate stream: word w of bond id takes half w mod 2 of the block
+// (t, class, id, w / 2).  Planes start at an even word when V >= 2.
+template <int V>
+__device__ __forceinline__ void graph_gates(uint32_t t, uint32_t cls, uint32_t id, uint32_t w0,
+                                            const RoundKeys& rk, uint64_t (&g)[V]) {
+  if constexpr (V == 1) {
+    const uint4 b = philox(make_uint4(t, cls, id, w0 >> 1), rk);
+    g[0] = (w0 & 1u) ? hi64(b) : lo64(b);
+  } else {
+#pragma unroll
+    for (int h = 0; h < V; h += 2) {
+      const uint4 b = philox(make_uint4(t, cls, id, (w0 + h) >> 1), rk);
+      g[h] = lo64(b);
+      g[h + 1] = hi64(b);
+    }
+  }
+}
+
+// The exchange on bond (u, v), V words: counts of the other neighbours of
+// u and of v, the rule, the gated swap, and the persistence update.
+template <int V, int M>
+__device__ __forceinline__ void exchange(uint64_t* np, uint64_t* pp, int z, int32_t u, int32_t v,
+                                         const int32_t (&ru)[kMaxZ], const int32_t (&rv)[kMaxZ],
+                                         const uint64_t (&g)[V]) {
   uint64_t nu[V], nv[V];
   ld<V>(np, u, nu);
   ld<V>(np, v, nv);
   uint64_t cu2[V], cu1[V], cu0[V], cv2[V], cv1[V], cv0[V];
 #pragma unroll
   for (int h = 0; h < V; ++h) cu2[h] = cu1[h] = cu0[h] = cv2[h] = cv1[h] = cv0[h] = 0;
-  for (int k = 0; k < z; ++k) {
-    const int32_t wu = a.nbr[(int64_t)u * z + k];
-    const int32_t wv = a.nbr[(int64_t)v * z + k];
-    uint64_t xu[V], xv[V];
-    ld<V>(np, wu, xu);
-    ld<V>(np, wv, xv);
-    const uint64_t keep_u = (wu != v) ? ~0ull : 0ull;  // skip the partner
-    const uint64_t keep_v = (wv != u) ? ~0ull : 0ull;
 #pragma unroll
-    for (int h = 0; h < V; ++h) {
-      add3(cu2[h], cu1[h], cu0[h], xu[h] & keep_u);
-      add3(cv2[h], cv1[h], cv0[h], xv[h] & keep_v);
-    }
-  }
-  // gate words.  Graphs: block (t, class, edge, word pair), half = word
-  // parity.  Cubic lattices (one-word planes): bonds of classes 4g+2b and
-  // 4g+2b+1 that start at neighbouring pencil positions share the block
-  // (t, 4g+2b, base site of the first, word), half = class parity.
-  uint64_t g[V];
-  if (a.pair_stride != 0) {
-    const uint32_t odd = a.cls & 1u;
+  for (int k = 0; k < kMaxZ; ++k) {
+    if (k < z) {
+      if (ru[k] != v) {  // the partner is not one of the "other" neighbours
+        uint64_t x[V];
+        ld<V>(np, ru[k], x);
 #pragma unroll
-    for (int h = 0; h < V; ++h) {
-      const uint4 b = philox(
-          make_uint4(a.t, a.cls - odd, id - odd * a.pair_stride, (uint32_t)(q * V + h)), a.rk);
-      g[h] = odd ? hi64(b) : lo64(b);
-    }
-  } else {
-    uint32_t c3, half;
-    if constexpr (V == 2) {
-      c3 = (uint32_t)q;
-      half = 0;
-    } else {
-      c3 = (uint32_t)(q >> 1);
-      half = (uint32_t)(q & 1);
-    }
-    const uint4 b = philox(make_uint4(a.t, a.cls, id, c3), a.rk);
-    if constexpr (V == 2) {
-      g[0] = lo64(b);
-      g[1] = hi64(b);
-    } else {
-      g[0] = half ? hi64(b) : lo64(b);
+        for (int h = 0; h < V; ++h) add3(cu2[h], cu1[h], cu0[h], x[h]);
+      }
+      if (rv[k] != u) {
+        uint64_t x[V];
+        ld<V>(np, rv[k], x);
+#pragma unroll
+        for (int h = 0; h < V; ++h) add3(cv2[h], cv1[h], cv0[h], x[h]);
+      }
     }
   }
   uint64_t sw[V];
@@ -156,14 +186,95 @@ __global__ void __launch_bounds__(256) k_graph_class(const ClassArgs a) {
   }
 }
 
+template <int V, int M>
+__global__ void __launch_bounds__(256) k_graph_class(const __grid_constant__ ClassArgs a) {
+  pdl_trigger();
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.count) return;
+  const int q = blockIdx.y;
+  uint64_t* np = a.n + (size_t)q * a.plane_elems;
+  uint64_t* pp = a.p + (size_t)q * a.plane_elems;
+  const int32_t u = a.bu[e], v = a.bv[e];
+  const uint32_t id = a.bid[e];
+  int32_t ru[kMaxZ], rv[kMaxZ];
+  load_row(a.nbr, a.z, u, ru);
+  load_row(a.nbr, a.z, v, rv);
+  // gate words.  Graphs: the graph stream.  Cubic lattices on this path:
+  // bonds of classes 4g+2b and 4g+2b+1 that start at neighbouring pencil
+  // positions share the block (t, 4g+2b, base site of the first, word),
+  // half = class parity.
+  uint64_t g[V];
+  const uint32_t w0 = (uint32_t)(q * V);
+  if (a.pair_stride != 0) {
+    const uint32_t odd = a.cls & 1u;
+#pragma unroll
+    for (int h = 0; h < V; ++h) {
+      const uint4 b = philox(make_uint4(a.t, a.cls - odd, id - odd * a.pair_stride, w0 + h), a.rk);
+      g[h] = odd ? hi64(b) : lo64(b);
+    }
+  } else {
+    graph_gates<V>(a.t, a.cls, id, w0, a.rk, g);
+  }
+  pdl_wait();
+  exchange<V, M>(np, pp, a.z, u, v, ru, rv, g);
+}
+
+// Batched form: one launch runs class c of every graph unit (one state plane
+// of one job); edges of all units are numbered consecutively, unit u owning
+// [prefix[u], prefix[u+1]) of them, which start at edge first[u] of its
+// class-ordered edge arrays.  Units whose sweep counter reached t_end skip.
+template <int V, int M>
+__global__ void __launch_bounds__(256) k_graph_class_batch(const GraphUnit* __restrict__ units,
+                                                           const int64_t* __restrict__ prefix,
+                                                           const int64_t* __restrict__ first,
+                                                           int nunits, uint32_t cls,
+                                                           uint32_t sweep_offset) {
+  pdl_trigger();
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= prefix[nunits]) return;
+  int lo = 0, hi = nunits - 1;  // last unit with prefix <= e
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= e) lo = mid; else hi = mid - 1;
+  }
+  const GraphUnit& gu = units[lo];
+  const uint32_t t = gu.t_base + sweep_offset;
+  if (t >= gu.t_end) return;
+  const int64_t k = first[lo] + (e - prefix[lo]);
+  const int32_t u = gu.bu[k], v = gu.bv[k];
+  const uint32_t id = gu.bid[k];
+  const int z = gu.z;
+  int32_t ru[kMaxZ], rv[kMaxZ];
+  load_row(gu.nbr, z, u, ru);
+  load_row(gu.nbr, z, v, rv);
+  uint64_t g[V];
+  graph_gates<V>(t, cls, id, gu.word0, gu.rk, g);
+  pdl_wait();
+  exchange<V, M>(gu.n, gu.p, z, u, v, ru, rv, g);
+}
+
+// launch with programmatic stream serialisation (see the file comment)
+template <typename... Exp, typename... Act>
+cudaError_t launch_pdl(void (*kern)(Exp...), dim3 grid, cudaStream_t s, Act&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Act>(args)...);
+}
+
 template <int V>
 cudaError_t launch_v(const ClassArgs& a, int m, dim3 grid, cudaStream_t s) {
-  const int mm = m < 7 ? m : 7;
-  switch (mm) {
-#define KA_CASE(MM)                                                   \
-  case MM:                                                            \
-    k_graph_class<V, MM><<<grid, 256, 0, s>>>(a);                     \
-    return cudaGetLastError();
+  switch (m < 7 ? m : 7) {
+#define KA_CASE(MM) \
+  case MM:          \
+    return launch_pdl(k_graph_class<V, MM>, grid, s, a);
     KA_CASE(0)
     KA_CASE(1)
     KA_CASE(2)
@@ -178,86 +289,26 @@ cudaError_t launch_v(const ClassArgs& a, int m, dim3 grid, cudaStream_t s) {
   }
 }
 
-// Batched form: one launch runs class c of every graph unit (one state plane
-// of one job); edges of all units are numbered consecutively, unit u owning
-// [prefix[u], prefix[u+1]) of them, which start at edge first[u] of its
-// class-ordered edge arrays.  Units whose sweep counter reached t_end skip.
-template <int V, int M>
-__global__ void __launch_bounds__(256) k_graph_class_batch(const GraphUnit* __restrict__ units,
-                                                           const int64_t* __restrict__ prefix,
-                                                           const int64_t* __restrict__ first,
-                                                           int nunits, uint32_t cls,
-                                                           uint32_t sweep_offset) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= prefix[nunits]) return;
-  int lo = 0, hi = nunits - 1;  // last unit with prefix <= e
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (prefix[mid] <= e) lo = mid; else hi = mid - 1;
-  }
-  const GraphUnit& gu = units[lo];
-  const uint32_t t = gu.t_base + sweep_offset;
-  if (t >= gu.t_end) return;
-  const int64_t k = first[lo] + (e - prefix[lo]);
-  uint64_t* np = gu.n;
-  uint64_t* pp = gu.p;
-  const int32_t u = gu.bu[k], v = gu.bv[k];
-  const uint32_t id = gu.bid[k];
-  const int z = gu.z;
-  uint64_t nu[V], nv[V];
-  ld<V>(np, u, nu);
-  ld<V>(np, v, nv);
-  uint64_t cu2[V], cu1[V], cu0[V], cv2[V], cv1[V], cv0[V];
-#pragma unroll
-  for (int h = 0; h < V; ++h) cu2[h] = cu1[h] = cu0[h] = cv2[h] = cv1[h] = cv0[h] = 0;
-  for (int q = 0; q < z; ++q) {
-    const int32_t wu = gu.nbr[(int64_t)u * z + q];
-    const int32_t wv = gu.nbr[(int64_t)v * z + q];
-    uint64_t xu[V], xv[V];
-    ld<V>(np, wu, xu);
-    ld<V>(np, wv, xv);
-    const uint64_t keep_u = (wu != v) ? ~0ull : 0ull;
-    const uint64_t keep_v = (wv != u) ? ~0ull : 0ull;
-#pragma unroll
-    for (int h = 0; h < V; ++h) {
-      add3(cu2[h], cu1[h], cu0[h], xu[h] & keep_u);
-      add3(cv2[h], cv1[h], cv0[h], xv[h] & keep_v);
-    }
-  }
-  // graph gate stream: block (t, class, edge, word pair), half = word parity
-  uint64_t g[V];
-  const uint32_t w0 = gu.word0;
-  if constexpr (V == 2) {
-    const uint4 b = philox(make_uint4(t, cls, id, w0 >> 1), gu.rk);
-    g[0] = lo64(b);
-    g[1] = hi64(b);
-  } else {
-    const uint4 b = philox(make_uint4(t, cls, id, w0 >> 1), gu.rk);
-    g[0] = (w0 & 1u) ? hi64(b) : lo64(b);
-  }
-  uint64_t sw[V];
-  bool any = false;
-#pragma unroll
-  for (int h = 0; h < V; ++h) {
-    const uint64_t ok = le3<M>(cu2[h], cu1[h], cu0[h]) & le3<M>(cv2[h], cv1[h], cv0[h]);
-    sw[h] = (nu[h] ^ nv[h]) & g[h] & ok;
-    nu[h] ^= sw[h];
-    nv[h] ^= sw[h];
-    any |= (sw[h] != 0);
-  }
-  if (any) {
-    st<V>(np, u, nu);
-    st<V>(np, v, nv);
-    uint64_t pu[V], pv[V];
-    ld<V>(pp, u, pu);
-    ld<V>(pp, v, pv);
-#pragma unroll
-    for (int h = 0; h < V; ++h) {
-      pu[h] &= ~sw[h];
-      pv[h] &= ~sw[h];
-    }
-    st<V>(pp, u, pu);
-    st<V>(pp, v, pv);
+template <int V>
+cudaError_t launch_batch_v(const GraphUnit* units, const int64_t* prefix, const int64_t* first,
+                           int nunits, int m, uint32_t cls, uint32_t off, dim3 grid,
+                           cudaStream_t s) {
+  switch (m < 7 ? m : 7) {
+#define KA_CASE(MM)                                                                     \
+  case MM:                                                                              \
+    return launch_pdl(k_graph_class_batch<V, MM>, grid, s, units, prefix, first, nunits, \
+                      cls, off);
+    KA_CASE(0)
+    KA_CASE(1)
+    KA_CASE(2)
+    KA_CASE(3)
+    KA_CASE(4)
+    KA_CASE(5)
+    KA_CASE(6)
+    KA_CASE(7)
+#undef KA_CASE
+    default:
+      return cudaErrorInvalidValue;
   }
 }
 
@@ -268,19 +319,13 @@ cudaError_t launch_graph_class_batch(const GraphUnit* units_dev, const int64_t* 
                                      int V, int m, uint32_t cls, uint32_t sweep_offset,
                                      cudaStream_t s) {
   if (nunits <= 0 || total_edges <= 0) return cudaSuccess;
-  const unsigned grid = (unsigned)((total_edges + 255) / 256);
-  const int mm = m < 7 ? m : 7;
-#define KA_CASE(VV, MM)                                                                  \
-  if (V == VV && mm == MM) {                                                             \
-    k_graph_class_batch<VV, MM><<<grid, 256, 0, s>>>(units_dev, prefix_dev, first_dev,   \
-                                                     nunits, cls, sweep_offset);         \
-    return cudaGetLastError();                                                           \
-  }
-  KA_CASE(1, 0) KA_CASE(1, 1) KA_CASE(1, 2) KA_CASE(1, 3) KA_CASE(1, 4) KA_CASE(1, 5)
-  KA_CASE(1, 6) KA_CASE(1, 7)
-  KA_CASE(2, 0) KA_CASE(2, 1) KA_CASE(2, 2) KA_CASE(2, 3) KA_CASE(2, 4) KA_CASE(2, 5)
-  KA_CASE(2, 6) KA_CASE(2, 7)
-#undef KA_CASE
+  const dim3 grid((unsigned)((total_edges + 255) / 256));
+  if (V == 4)
+    return launch_batch_v<4>(units_dev, prefix_dev, first_dev, nunits, m, cls, sweep_offset, grid, s);
+  if (V == 2)
+    return launch_batch_v<2>(units_dev, prefix_dev, first_dev, nunits, m, cls, sweep_offset, grid, s);
+  if (V == 1)
+    return launch_batch_v<1>(units_dev, prefix_dev, first_dev, nunits, m, cls, sweep_offset, grid, s);
   return cudaErrorInvalidValue;
 }
 
@@ -306,8 +351,10 @@ cudaError_t launch_graph_class(const Planes& pl, const GraphDev& g, int64_t off,
     a.pair_stride = s;
   }
   a.rk = rk;
-  dim3 grid((unsigned)((count + 255) / 256), (unsigned)pl.P);
-  return pl.V == 2 ? launch_v<2>(a, g.m, grid, s) : launch_v<1>(a, g.m, grid, s);
+  const dim3 grid((unsigned)((count + 255) / 256), (unsigned)pl.P);
+  if (pl.V == 4) return launch_v<4>(a, g.m, grid, s);
+  if (pl.V == 2) return launch_v<2>(a, g.m, grid, s);
+  return launch_v<1>(a, g.m, grid, s);
 }
 
 }  // namespace ka

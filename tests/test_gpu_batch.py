@@ -27,6 +27,7 @@ JOBS = [
     dict(params=dict(topo=K.KA_RRG, N=4096, z=4, m=2, replicas=64, graph_seed=1), sweeps=30, every=10, seed=10, rho=0.78),
     dict(params=dict(topo=K.KA_RRG, N=2048, z=4, m=2, replicas=128, graph_seed=2), sweeps=17, every=6, seed=11, rho=0.82),
     dict(params=dict(topo=K.KA_RRG, N=1000, z=3, m=1, replicas=64, graph_seed=3), sweeps=14, every=14, seed=12, rho=0.7),
+    dict(params=dict(topo=K.KA_RRG, N=3000, z=4, m=2, replicas=256, graph_seed=4), sweeps=13, every=5, seed=14, rho=0.8),
     dict(params=dict(topo=K.KA_CUBIC, d=3, L=8, m=3, replicas=64, flags=K.KA_FLAG_GENERIC), sweeps=11, every=3, seed=13, rho=0.7),
 ]
 

@@ -98,6 +98,8 @@ RRG = [
     dict(N=1000, z=3, m=1, replicas=128),
     dict(N=500, z=6, m=3, replicas=192),
     dict(N=2000, z=4, m=3, replicas=256),
+    dict(N=3000, z=4, m=2, replicas=512),   # four-word planes, two of them
+    dict(N=1024, z=3, m=1, replicas=256),
 ]
 
 
