@@ -340,7 +340,6 @@ def _run_batch(jobs, flags, dev, k):
     rounds = 0
     if k == 0 and not (flags & K.KA_BATCH_PLAIN):
         k = b.autotune()  # times real rounds of this batch: part of the timed work
-        rounds += 3
     while b.info()["active"]:
         b.step(k or 16)
         rounds += 1

@@ -249,8 +249,10 @@ ka_status ka_batch_adopt(ka_batch *b, ka_ctx *ctx, const ka_job_spec *spec, int6
  * the due observations.  *sweeps_run = the round's length.  Synchronises. */
 ka_status ka_batch_step(ka_batch *b, int64_t max_sweeps, int64_t *sweeps_run);
 
-/* Time a few round lengths on the live batch (the rounds do real work) and
- * keep the fastest for ka_batch_step(b, 0, ...).  *best_round may be NULL. */
+/* Time a few round lengths (4, 16, 64 sweeps) on the live batch and keep
+ * the fastest for ka_batch_step(b, 0, ...).  Each length first runs warm-up
+ * rounds (tables; in graph mode the capture), then one timed round; all
+ * these rounds do real work.  *best_round may be NULL. */
 ka_status ka_batch_autotune(ka_batch *b, int64_t *best_round);
 
 /* Progress of a job. */

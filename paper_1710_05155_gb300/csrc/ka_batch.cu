@@ -75,7 +75,9 @@ struct ka_batch {
   int32_t flags = 0;
   int64_t next_id = 1;
   std::map<int64_t, Job*> jobs;
-  bool dirty = true;
+  bool dirty = true;         // jobs were added: the tables must be rebuilt
+  int64_t units = 0;         // units in the tables
+  int64_t idle_units = 0;    // of which belong to finished or removed jobs
   std::vector<CubicClass> cubic;
   std::vector<GraphClass> graph;
   std::vector<void*> table_mem;  // device tables of the current job set
@@ -227,6 +229,10 @@ cudaError_t rebuild(ka_batch* b) {
   }
   b->dirty = false;
   b->last_k = 0;
+  b->units = 0;
+  for (auto& cc : b->cubic) b->units += (int64_t)cc.units.size();
+  for (auto& gc : b->graph) b->units += (int64_t)gc.units.size();
+  b->idle_units = 0;
   return cudaStreamSynchronize(b->stream);
 }
 
@@ -279,7 +285,10 @@ ka_status observe_job(ka_batch* b, Job* j) {
 }
 
 ka_status run_round(ka_batch* b, int64_t k_req, int64_t* ran) {
-  if (b->dirty) {
+  // finished and removed jobs stay in the tables as idle units (their
+  // launches skip them) until they are half of all units; new jobs need a
+  // rebuild at once
+  if (b->dirty || 2 * b->idle_units > b->units) {
     cudaError_t e = rebuild(b);
     if (e) return cuda_err(b, e, "batch tables");
   }
@@ -305,8 +314,9 @@ ka_status run_round(ka_batch* b, int64_t k_req, int64_t* ran) {
     for (auto& cc : b->cubic) {
       for (size_t u = 0; u < cc.units.size(); ++u) {
         const Job* j = cc.owner[u];
-        cc.units[u].t_base = (uint32_t)j->t;
-        cc.units[u].t_end = (uint32_t)(j->t + allowance(j, k));
+        const bool live = j && !j->finished;
+        cc.units[u].t_base = live ? (uint32_t)j->t : 0u;
+        cc.units[u].t_end = live ? (uint32_t)(j->t + allowance(j, k)) : 0u;
       }
       if ((e = cudaMemcpyAsync(cc.dev, cc.units.data(), cc.units.size() * sizeof(ka::CubicUnit),
                                cudaMemcpyHostToDevice, b->stream)))
@@ -315,8 +325,9 @@ ka_status run_round(ka_batch* b, int64_t k_req, int64_t* ran) {
     for (auto& gc : b->graph) {
       for (size_t u = 0; u < gc.units.size(); ++u) {
         const Job* j = gc.owner[u];
-        gc.units[u].t_base = (uint32_t)j->t;
-        gc.units[u].t_end = (uint32_t)(j->t + allowance(j, k));
+        const bool live = j && !j->finished;
+        gc.units[u].t_base = live ? (uint32_t)j->t : 0u;
+        gc.units[u].t_end = live ? (uint32_t)(j->t + allowance(j, k)) : 0u;
       }
       if ((e = cudaMemcpyAsync(gc.dev, gc.units.data(), gc.units.size() * sizeof(ka::GraphUnit),
                                cudaMemcpyHostToDevice, b->stream)))
@@ -369,7 +380,7 @@ ka_status run_round(ka_batch* b, int64_t k_req, int64_t* ran) {
     }
     if (j->t >= j->target) {
       j->finished = true;
-      b->dirty = true;
+      if (j->batched) b->idle_units += j->ctx->pl.P;  // idles in the tables until rebuilt
     }
   }
   e = cudaStreamSynchronize(b->stream);
@@ -533,22 +544,21 @@ ka_status ka_batch_autotune(ka_batch* b, int64_t* best_round) {
   cudaEventCreate(&e1);
   ka_status st = KA_OK;
   for (int64_t k : cand) {
-    // work of this round: site-words times sweeps over the unfinished jobs
+    // warm-up rounds of length k: the first builds the tables, and in graph
+    // mode the second captures the round (a length is captured on its second
+    // use); the next round is timed as the steady state
+    int64_t ran = 0;
+    const int warm = (b->flags & KA_BATCH_GRAPH) ? 2 : 1;
+    for (int w = 0; w < warm && !st; ++w) st = run_round(b, k, &ran);
+    if (st || ran == 0) break;
+    // work of the timed round: site-words times sweeps over the unfinished jobs
     double work = 0.0;
     for (auto& kv : b->jobs) {
       const Job* j = kv.second;
       if (!j->finished) work += (double)j->ctx->N * (j->ctx->R / 64) * (double)allowance(j, k);
     }
     if (work == 0.0) break;
-    if (b->dirty) {  // table rebuild outside the timed region
-      cudaError_t e = rebuild(b);
-      if (e) {
-        st = cuda_err(b, e, "batch tables");
-        break;
-      }
-    }
     cudaEventRecord(e0, b->stream);
-    int64_t ran = 0;
     st = run_round(b, k, &ran);
     cudaEventRecord(e1, b->stream);
     cudaEventSynchronize(e1);
@@ -602,12 +612,26 @@ ka_status ka_batch_remove(ka_batch* b, int64_t job_id) {
   if (it == b->jobs.end()) return KA_EINVAL;
   Job* j = it->second;
   cudaStreamSynchronize(b->stream);
+  // its units (if any) stay in the tables as idle units, with no owner
+  int64_t in_tables = 0;
+  for (auto& cc : b->cubic)
+    for (auto& o : cc.owner)
+      if (o == j) {
+        o = nullptr;
+        ++in_tables;
+      }
+  for (auto& gc : b->graph)
+    for (auto& o : gc.owner)
+      if (o == j) {
+        o = nullptr;
+        ++in_tables;
+      }
+  if (!j->finished) b->idle_units += in_tables;
   const ka_status st = ka_destroy(j->ctx);  // frees the context's buffer
   cudaFree(j->obs_dev);
   b->used -= j->bytes;
   b->jobs.erase(it);
   delete j;
-  b->dirty = true;
   return st;
 }
 

@@ -401,11 +401,19 @@ __global__ void __launch_bounds__(kThreads, KA_CUBIC_MIN_BLOCKS)
     if (threadIdx.x < pm.count) build_info<D, V, X>(a, pm, threadIdx.x, info[b][threadIdx.x]);
   };
 
-  // prologue: the CTA's first tile
+  // prologue: the CTA's first tile.  Single-instance launches are chained
+  // with programmatic dependent launch: the next group may start as soon as
+  // every CTA of this one runs, and this one prepares its first tile (static
+  // tables only) before waiting for the previous group to finish writing the
+  // state.  Without that launch attribute the wait returns at once.  The
+  // batched form never lets a dependent start early: a waiting grid would
+  // share the SMs with this one for its whole run.
+  if constexpr (!B) asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   uint32_t tile = blockIdx.x;
   PencilMap<D, V, X> pm;
   prepare(tile, 0, pm);
   __syncthreads();
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
   issue(args(0), pm, 0);
 
   for (int it = 0; tile < ntiles; ++it) {
@@ -563,10 +571,13 @@ struct LaunchCache {
   int per_sm[kDevices] = {}, sms[kDevices] = {};
 };
 
-// Launch a persistent grid: at most as many CTAs as fit on the device at once.
+// Launch a persistent grid (at most as many CTAs as fit on the device at
+// once), with programmatic stream serialisation if pdl.  Single-instance
+// sweeps use it (a group's first tile is prepared while the previous group
+// drains); batched rounds do not, where it measured slower.
 template <typename Kern>
 cudaError_t launch_persistent(Kern kern, LaunchCache& lc, const GroupArgs& a, const BatchArgs& ba,
-                              unsigned blocks, size_t smem, cudaStream_t st) {
+                              unsigned blocks, size_t smem, cudaStream_t st, bool pdl) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -589,8 +600,17 @@ cudaError_t launch_persistent(Kern kern, LaunchCache& lc, const GroupArgs& a, co
     }
     cap = (unsigned)(lc.per_sm[dev] * lc.sms[dev]);
   }
-  kern<<<blocks < cap ? blocks : cap, kThreads, smem, st>>>(a, ba);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks < cap ? blocks : cap);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a, ba);
 }
 
 template <int D, int V, bool X, bool B>
@@ -604,7 +624,7 @@ cudaError_t launch_dx(const GroupArgs& a, const BatchArgs& ba, int m, unsigned b
     if constexpr (MM <= Z - 1) {                                                       \
       static LaunchCache lc;                                                           \
       return launch_persistent(k_cubic_group<D, V, MM, X, B>, lc, a, ba, blocks, smem, \
-                               st);                                                    \
+                               st, !B);                                                \
     }                                                                                  \
     break;
     KA_CASE(0)

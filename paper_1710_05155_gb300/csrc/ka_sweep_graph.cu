@@ -11,13 +11,12 @@
 // A plane holds V = 1, 2 or 4 words per site, so a site's words share one
 // 32-byte sector: every gather is a random access, and the sector is the
 // unit the memory system moves.  The partner's word is not gathered twice.
-//
-// Classes run as consecutive launches with programmatic dependent launch:
-// a class launch may start while the previous one drains, and does all the
-// work that reads only static tables (its bond, the two neighbour rows, the
-// gate words) before it waits for the previous class to complete.
-#include <utility>
-
+// A thread first loads what depends only on static tables (its bond, the
+// two neighbour rows) and computes the gate words, then gathers the state.
+// Single-instance class launches are chained with programmatic dependent
+// launch, so that this prologue overlaps the previous class's tail (small
+// graphs are bound by launch latency); batched launches are not, since a
+// grid waiting on the SMs slows the one it waits for.
 #include "ka_internal.cuh"
 
 namespace ka {
@@ -87,13 +86,6 @@ __device__ __forceinline__ void st(uint64_t* base, int64_t i, const uint64_t (&o
       *reinterpret_cast<ulonglong2*>(base + V * i + h) = make_ulonglong2(o[h], o[h + 1]);
   }
 }
-
-// programmatic dependent launch: let the next class launch start, and wait
-// for the previous one before touching the state
-__device__ __forceinline__ void pdl_trigger() {
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-}
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 
 constexpr int kMaxZ = 8;
 
@@ -188,7 +180,7 @@ __device__ __forceinline__ void exchange(uint64_t* np, uint64_t* pp, int z, int3
 
 template <int V, int M>
 __global__ void __launch_bounds__(256) k_graph_class(const __grid_constant__ ClassArgs a) {
-  pdl_trigger();
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= a.count) return;
   const int q = blockIdx.y;
@@ -215,7 +207,7 @@ __global__ void __launch_bounds__(256) k_graph_class(const __grid_constant__ Cla
   } else {
     graph_gates<V>(a.t, a.cls, id, w0, a.rk, g);
   }
-  pdl_wait();
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");  // the previous class is complete
   exchange<V, M>(np, pp, a.z, u, v, ru, rv, g);
 }
 
@@ -229,7 +221,6 @@ __global__ void __launch_bounds__(256) k_graph_class_batch(const GraphUnit* __re
                                                            const int64_t* __restrict__ first,
                                                            int nunits, uint32_t cls,
                                                            uint32_t sweep_offset) {
-  pdl_trigger();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= prefix[nunits]) return;
   int lo = 0, hi = nunits - 1;  // last unit with prefix <= e
@@ -249,13 +240,12 @@ __global__ void __launch_bounds__(256) k_graph_class_batch(const GraphUnit* __re
   load_row(gu.nbr, z, v, rv);
   uint64_t g[V];
   graph_gates<V>(t, cls, id, gu.word0, gu.rk, g);
-  pdl_wait();
   exchange<V, M>(gu.n, gu.p, z, u, v, ru, rv, g);
 }
 
-// launch with programmatic stream serialisation (see the file comment)
-template <typename... Exp, typename... Act>
-cudaError_t launch_pdl(void (*kern)(Exp...), dim3 grid, cudaStream_t s, Act&&... args) {
+// single-instance launch with programmatic stream serialisation
+template <typename Kern>
+cudaError_t launch_pdl(Kern kern, dim3 grid, cudaStream_t s, const ClassArgs& a) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = dim3(256);
@@ -266,7 +256,7 @@ cudaError_t launch_pdl(void (*kern)(Exp...), dim3 grid, cudaStream_t s, Act&&...
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, std::forward<Act>(args)...);
+  return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 template <int V>
@@ -296,8 +286,8 @@ cudaError_t launch_batch_v(const GraphUnit* units, const int64_t* prefix, const 
   switch (m < 7 ? m : 7) {
 #define KA_CASE(MM)                                                                     \
   case MM:                                                                              \
-    return launch_pdl(k_graph_class_batch<V, MM>, grid, s, units, prefix, first, nunits, \
-                      cls, off);
+    k_graph_class_batch<V, MM><<<grid, 256, 0, s>>>(units, prefix, first, nunits, cls, off); \
+    return cudaGetLastError();
     KA_CASE(0)
     KA_CASE(1)
     KA_CASE(2)
