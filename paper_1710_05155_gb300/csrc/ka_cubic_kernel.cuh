@@ -341,9 +341,8 @@ __global__ void __launch_bounds__(kThreads, KA_CUBIC_MIN_BLOCKS)
   __shared__ PencilInfo<D> info[2][TP];
   __shared__ GroupArgs sargs[B ? 2 : 1];
   __shared__ uint32_t slocal[B ? 2 : 1];
-  auto args = [&](int b) -> const GroupArgs& {
-    if constexpr (B) return sargs[b]; else return la;
-  };
+  // the arguments of buffer b's tile: the unit's (batched) or the launch's
+#define KA_TILE_ARGS(b) (B ? sargs[(b)] : la)
 
   // shared memory of buffer b: array a (0 = n, 1 = p, 2.. = neighbours), word
   // h is the plane [(a V + h)][TP][PSmax]
@@ -396,7 +395,7 @@ __global__ void __launch_bounds__(kThreads, KA_CUBIC_MIN_BLOCKS)
       }
       local = slocal[b];
     }
-    const GroupArgs& a = args(b);
+    const GroupArgs& a = KA_TILE_ARGS(b);
     pm.init(a, local);
     if (threadIdx.x < pm.count) build_info<D, V, X>(a, pm, threadIdx.x, info[b][threadIdx.x]);
   };
@@ -414,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, KA_CUBIC_MIN_BLOCKS)
   prepare(tile, 0, pm);
   __syncthreads();
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
-  issue(args(0), pm, 0);
+  issue(KA_TILE_ARGS(0), pm, 0);
 
   for (int it = 0; tile < ntiles; ++it) {
     const int b = it & 1;
@@ -426,14 +425,14 @@ __global__ void __launch_bounds__(kThreads, KA_CUBIC_MIN_BLOCKS)
     __syncthreads();
     // start the next tile's copies, then wait for this tile's
     if (more) {
-      issue(args(b ^ 1), pn, b ^ 1);
+      issue(KA_TILE_ARGS(b ^ 1), pn, b ^ 1);
       asm volatile("cp.async.wait_group 1;\n" ::: "memory");
     } else {
       asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     }
     __syncthreads();
 
-    const GroupArgs& a = args(b);
+    const GroupArgs& a = KA_TILE_ARGS(b);
     const int L = a.L, PS = a.PS;
     const uint32_t smu = (uint32_t)a.st[a.mu];
     const int count = pm.count;
@@ -460,7 +459,7 @@ __global__ void __launch_bounds__(kThreads, KA_CUBIC_MIN_BLOCKS)
         const uint4 g01 = philox(make_uint4(a.t, a.cls0, s0, word), a.rk);
         const uint4 g23 = philox(make_uint4(a.t, a.cls0 + 2, s0 + 2 * smu, word), a.rk);
         int e[4];
-        uint64_t nn[4], A[4], B[4], fl[4];
+        uint64_t nn[4], mA[4], mB[4], fl[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           e[k] = j * PS + slot(4 * seg + k);
@@ -470,16 +469,16 @@ __global__ void __launch_bounds__(kThreads, KA_CUBIC_MIN_BLOCKS)
           for (int q = 0; q < KP; ++q) xs[q] = splane(b, 2 + q, h)[e[k]];
           uint64_t b2, b1, b0;
           count_perp<KP>(xs, b2, b1, b0);
-          A[k] = le3<M - 1>(b2, b1, b0);
-          B[k] = le3<M>(b2, b1, b0);
+          mA[k] = le3<M - 1>(b2, b1, b0);
+          mB[k] = le3<M>(b2, b1, b0);
           fl[k] = 0;
         }
         // class 0: bond (s0, s1); s0's other along-neighbour is the previous
         // segment's s3 (still at its group-start value), s1's is s2
         {
           const uint64_t left = __shfl_sync(act, nn[3], prev);
-          const uint64_t ok0 = (left & A[0]) | (~left & B[0]);
-          const uint64_t ok1 = (nn[2] & A[1]) | (~nn[2] & B[1]);
+          const uint64_t ok0 = (left & mA[0]) | (~left & mB[0]);
+          const uint64_t ok1 = (nn[2] & mA[1]) | (~nn[2] & mB[1]);
           const uint64_t sw = (nn[0] ^ nn[1]) & lo64(g01) & ok0 & ok1;
           nn[0] ^= sw;
           nn[1] ^= sw;
@@ -488,8 +487,8 @@ __global__ void __launch_bounds__(kThreads, KA_CUBIC_MIN_BLOCKS)
         }
         // class 1: bond (s1, s2); other along-neighbours s0 and s3
         {
-          const uint64_t ok1 = (nn[0] & A[1]) | (~nn[0] & B[1]);
-          const uint64_t ok2 = (nn[3] & A[2]) | (~nn[3] & B[2]);
+          const uint64_t ok1 = (nn[0] & mA[1]) | (~nn[0] & mB[1]);
+          const uint64_t ok2 = (nn[3] & mA[2]) | (~nn[3] & mB[2]);
           const uint64_t sw = (nn[1] ^ nn[2]) & hi64(g01) & ok1 & ok2;
           nn[1] ^= sw;
           nn[2] ^= sw;
@@ -500,8 +499,8 @@ __global__ void __launch_bounds__(kThreads, KA_CUBIC_MIN_BLOCKS)
         // segment's s0, which only class 0 has written so far
         const uint64_t right = __shfl_sync(act, nn[0], next);
         {
-          const uint64_t ok2 = (nn[1] & A[2]) | (~nn[1] & B[2]);
-          const uint64_t ok3 = (right & A[3]) | (~right & B[3]);
+          const uint64_t ok2 = (nn[1] & mA[2]) | (~nn[1] & mB[2]);
+          const uint64_t ok3 = (right & mA[3]) | (~right & mB[3]);
           const uint64_t sw = (nn[2] ^ nn[3]) & lo64(g23) & ok2 & ok3;
           nn[2] ^= sw;
           nn[3] ^= sw;
@@ -511,9 +510,9 @@ __global__ void __launch_bounds__(kThreads, KA_CUBIC_MIN_BLOCKS)
         // class 3: bond (s3, next s0); the owner of next s0 evaluates that
         // site's condition (its other along-neighbour is its s1) and sends it
         {
-          const uint64_t mine = (nn[1] & A[0]) | (~nn[1] & B[0]);
+          const uint64_t mine = (nn[1] & mA[0]) | (~nn[1] & mB[0]);
           const uint64_t okn = __shfl_sync(act, mine, next);
-          const uint64_t ok3 = (nn[2] & A[3]) | (~nn[2] & B[3]);
+          const uint64_t ok3 = (nn[2] & mA[3]) | (~nn[2] & mB[3]);
           const uint64_t sw = (nn[3] ^ right) & hi64(g23) & ok3 & okn;
           nn[3] ^= sw;
           fl[3] |= sw;
@@ -560,6 +559,8 @@ __global__ void __launch_bounds__(kThreads, KA_CUBIC_MIN_BLOCKS)
     tile = nxt;
   }
 }
+
+#undef KA_TILE_ARGS
 
 // Per kernel instance and device: the dynamic shared memory granted so far
 // and the resident CTAs per SM at the last shared-memory size.  Guarded, as
