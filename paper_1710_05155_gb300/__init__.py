@@ -431,3 +431,17 @@ def correlation(counts: np.ndarray, N: int, K: int) -> float:
 def persistence(counts: np.ndarray, K: int) -> float:
     """Fraction of the initial particles whose site has never changed."""
     return float((counts[:, 2] / K).mean())
+
+
+def susceptibility(counts: np.ndarray, N: int, K: int) -> float:
+    """Dynamical susceptibility chi_4(t) of section 2.2: N times the variance, over
+    replicas (the average over initial configurations), of the overlap
+    q_r(t) = (sum_i n_i(t) n_i(0) - N rho^2) / (N rho (1 - rho)), rho = K / N.
+
+    counts: int64 [R, 4] as returned by ka_observe.  Replica averages are plain
+    means over the R replicas.  chi_4(0) = 0; for independent uniform
+    configurations (the ergodic long-time limit) its expectation is N / (N - 1).
+    """
+    rho = K / N
+    q = (counts[:, 1] - N * rho * rho) / (N * rho * (1.0 - rho))
+    return float(N * (np.mean(q * q) - np.mean(q) ** 2))

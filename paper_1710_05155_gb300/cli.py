@@ -4,9 +4,10 @@
         --rho 0.7 --sweeps 1000 --every 10
     python -m paper_1710_05155_gb300.cli --topo rrg --N 1048576 --z 4 --m 2 --rho 0.8 --sweeps 100
 
-One JSON line per observation: the sweep, the persistence phi(t) and the
-density autocorrelation C(t) averaged over replicas (section 2.2 and 3.3 of
-the paper; see ``correlation`` and ``persistence``), the mean particle count,
+One JSON line per observation: the sweep, the persistence phi(t), the
+density autocorrelation C(t) averaged over replicas and the dynamical
+susceptibility chi_4(t) (sections 2.2 and 3.3 of the paper; see
+``correlation``, ``persistence`` and ``susceptibility``), the mean particle count,
 and a final line with the device time of the sweeps.
 """
 from __future__ import annotations
@@ -15,7 +16,7 @@ import argparse
 import json
 import time
 
-from . import KA_CUBIC, KA_RRG, Simulation, correlation, ka_info, persistence
+from . import KA_CUBIC, KA_RRG, Simulation, correlation, ka_info, persistence, susceptibility
 
 
 def main(argv=None) -> None:
@@ -51,7 +52,7 @@ def main(argv=None) -> None:
 
     def emit(t, counts):
         print(json.dumps({"sweep": int(t), "phi": persistence(counts, K),
-                          "C": correlation(counts, N, K),
+                          "C": correlation(counts, N, K), "chi4": susceptibility(counts, N, K),
                           "particles": float(counts[:, 0].mean())}), flush=True)
 
     t, counts = sim.observe()
