@@ -73,6 +73,8 @@ def _load():
                                    I, I64, I64, u8p, u8p]
         lib.ora_observe.argtypes = [I64, I64, u8p, u8p, u8p, i64p]
         lib.ora_observe.restype = None
+        lib.ora_four_point.argtypes = [I, I, I64, u8p, u8p, I64, i64p, i64p]
+        lib.ora_four_point.restype = I
         for name in ("ora_cubic_tables", "ora_rrg_build", "ora_graph_edges", "ora_graph_classes",
                      "ora_check_schedule", "ora_local_move", "ora_init", "ora_class_step",
                      "ora_sweeps"):
@@ -229,6 +231,16 @@ def observe(st: State) -> np.ndarray:
     out = np.zeros((st.Rs, 4), np.int64)
     _load().ora_observe(st.N, st.Rs, st.n, st.n0, st.p, out)
     return out
+
+
+def four_point(d: int, L: int, st: State, smax: int):
+    """(phi int64 [Rs, smax+1], psi int64 [smax+1]): ordered site pairs by shell
+    s = |delta|^2 (components in [-L/2, L/2)), phi per replica of q_i q_j with
+    q = n AND n0, psi of M_i M_j with M_i = sum over replicas of q_i."""
+    phi = np.zeros((st.Rs, smax + 1), np.int64)
+    psi = np.zeros(smax + 1, np.int64)
+    _check(_load().ora_four_point(d, L, st.Rs, st.n, st.n0, smax, phi, psi), "four_point")
+    return phi, psi
 
 
 def pack_words(bits: np.ndarray) -> np.ndarray:

@@ -634,3 +634,38 @@ void ora_observe(int64_t N, int64_t Rs, const uint8_t *n, const uint8_t *n0, con
         counts[rr * 4 + 3] = persist_all;
     }
 }
+
+int ora_four_point(int d, int L, int64_t Rs, const uint8_t *n, const uint8_t *n0, int64_t smax,
+                   int64_t *phi, int64_t *psi)
+{
+    if (d < 1 || d > 4 || L < 2 || L % 2 || Rs < 1 || smax < 0) return 1;
+    int64_t N = 1;
+    for (int k = 0; k < d; k++) N *= L;
+    for (int64_t x = 0; x < Rs * (smax + 1); x++) phi[x] = 0;
+    for (int64_t s = 0; s <= smax; s++) psi[s] = 0;
+    int64_t *M = (int64_t *)calloc((size_t)N, sizeof(int64_t));
+    if (!M) return 2;
+    for (int64_t i = 0; i < N; i++)
+        for (int64_t rr = 0; rr < Rs; rr++) M[i] += n[i * Rs + rr] & n0[i * Rs + rr];
+    for (int64_t i = 0; i < N; i++) {
+        for (int64_t j = 0; j < N; j++) {
+            /* shell of the pair: squared norm of the representative displacement */
+            int64_t s = 0, a = i, b = j;
+            for (int k = 0; k < d; k++) {
+                int64_t dx = (b % L) - (a % L);
+                a /= L;
+                b /= L;
+                if (dx < -L / 2) dx += L;
+                if (dx >= L / 2) dx -= L;
+                s += dx * dx;
+            }
+            if (s > smax) continue;
+            psi[s] += M[i] * M[j];
+            for (int64_t rr = 0; rr < Rs; rr++)
+                phi[rr * (smax + 1) + s] +=
+                    (n[i * Rs + rr] & n0[i * Rs + rr]) & (n[j * Rs + rr] & n0[j * Rs + rr]);
+        }
+    }
+    free(M);
+    return 0;
+}

@@ -90,6 +90,17 @@ int ora_sweeps(int64_t N, int z, const int32_t *nbr, int m, int64_t nclass,
 void ora_observe(int64_t N, int64_t Rs, const uint8_t *n, const uint8_t *n0,
                  const uint8_t *p, int64_t *counts);
 
+/* Four-point correlations on the periodic cubic lattice (section 2.2 g_4(r,t),
+ * section 3.3 Phi(r,t)), by brute force over all ordered site pairs (i, j).
+ * The displacement of a pair is taken with every component in [-L/2, L/2)
+ * (one representative per class modulo L) and its shell is s = |delta|^2.
+ * With q_i = n_i AND n0_i per replica and M_i = sum over replicas of q_i:
+ *   phi[rr * (smax + 1) + s] = sum over pairs in shell s of q_i q_j (replica rr)
+ *   psi[s]                   = sum over pairs in shell s of M_i M_j
+ * for s = 0 .. smax; pairs in shells above smax are not counted. */
+int ora_four_point(int d, int L, int64_t Rs, const uint8_t *n, const uint8_t *n0, int64_t smax,
+                   int64_t *phi, int64_t *psi);
+
 #ifdef __cplusplus
 }
 #endif

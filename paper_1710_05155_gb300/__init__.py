@@ -445,3 +445,16 @@ def susceptibility(counts: np.ndarray, N: int, K: int) -> float:
     rho = K / N
     q = (counts[:, 1] - N * rho * rho) / (N * rho * (1.0 - rho))
     return float(N * (np.mean(q * q) - np.mean(q) ** 2))
+
+
+def four_point_g4(phi: np.ndarray, psi: np.ndarray, N: int, K: int) -> np.ndarray:
+    """g_4(r, t) of section 2.2 per shell s = r^2, from ka_four_point's outputs.
+
+    g4[s] = sum over ordered pairs (i, j) in shell s of (<q_i q_j> - <q_i><q_j>),
+    divided by N rho^2 (1 - rho)^2, with <.> the mean over the R replicas:
+    <q_i q_j> summed over the shell is phi[:, s].sum() / R and <q_i><q_j> is
+    psi[s] / R^2.  Summed over every shell of the lattice it equals chi_4(t).
+    """
+    R = phi.shape[0]
+    rho = K / N
+    return (phi.sum(axis=0) / R - psi / (R * R)) / (N * rho * rho * (1.0 - rho) ** 2)
