@@ -150,6 +150,24 @@ ka_status ka_observe(ka_ctx *ctx, int64_t *sweep_out, int64_t *counts);
  * synchronisation. */
 ka_status ka_observe_device(ka_ctx *ctx, int64_t *counts_device);
 
+/* Four-point correlations of a cubic lattice (section 2.2 g_4(r, t); section
+ * 3.3 Phi(r, t)) between the current state and the initial one.  With
+ * q_i = n_i AND n0_i per replica and M_i = the number of replicas with
+ * q_i = 1, every ordered site pair (i, j) is counted once, in the shell
+ * s = |delta|^2 of the representative of its displacement with every
+ * component in [-L/2, L/2):
+ *   phi[r * (smax + 1) + s] = sum over pairs in shell s of q_i q_j  (replica r)
+ *   psi[s]                  = sum over pairs in shell s of M_i M_j
+ * for s = 0 .. smax (shells without lattice vectors stay 0; pairs beyond
+ * smax are not counted).  g_4 of shell s is (sum_r phi[r][s] / R - psi[s] /
+ * R^2) / (N rho^2 (1 - rho)^2); summed over all shells it is chi_4.
+ * phi: host int64 [R][smax + 1], required; psi: host int64 [smax + 1] or
+ * NULL.  0 <= smax <= d (L/2)^2 and at most 65536 displacement vectors with
+ * |delta|^2 <= smax, else KA_EINVAL; KA_EINVAL on graphs, KA_ESTATE before
+ * init.  Uses stream-ordered scratch memory on the context's device,
+ * released before return; synchronises the stream. */
+ka_status ka_four_point(ka_ctx *ctx, int32_t smax, int64_t *phi, int64_t *psi);
+
 /* Copy the state to host arrays in canonical layout [R/64][N] uint64 each
  * (word-plane major).  Any pointer may be NULL.  Synchronises. */
 ka_status ka_get_state(ka_ctx *ctx, uint64_t *n, uint64_t *n0, uint64_t *p);

@@ -80,6 +80,7 @@ _SIGS = {
     "ka_batch_create": (C.c_int, [C.c_int32, C.c_void_p, C.c_size_t, C.c_int32, _P(C.c_void_p)]),
     "ka_batch_add": (C.c_int, [C.c_void_p, _P(ka_params), _P(ka_job_spec), _P(C.c_int64)]),
     "ka_job_bytes": (C.c_int, [_P(ka_params), _P(ka_job_spec), _P(C.c_size_t)]),
+    "ka_four_point": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "ka_batch_adopt": (C.c_int, [C.c_void_p, C.c_void_p, _P(ka_job_spec), _P(C.c_int64)]),
     "ka_batch_step": (C.c_int, [C.c_void_p, C.c_int64, _P(C.c_int64)]),
     "ka_batch_autotune": (C.c_int, [C.c_void_p, _P(C.c_int64)]),
@@ -204,6 +205,17 @@ def ka_observe(ctx: Ctx, out: np.ndarray | None = None):
     sweep = C.c_int64(0)
     _check(load().ka_observe(ctx.handle, C.byref(sweep), _ptr(out)), "ka_observe", ctx)
     return sweep.value, out
+
+
+def ka_four_point(ctx: Ctx, smax: int, with_psi: bool = True):
+    """(phi int64 [R, smax+1], psi int64 [smax+1] or None): four-point sums by shell
+    s = |delta|^2 (section 2.2 g_4, section 3.3 Phi); see include/ka.h."""
+    R = ka_info(ctx)["replicas"]
+    phi = np.zeros((R, smax + 1), np.int64)
+    psi = np.zeros(smax + 1, np.int64) if with_psi else None
+    _check(load().ka_four_point(ctx.handle, smax, _ptr(phi), _ptr(psi) if with_psi else None),
+           "ka_four_point", ctx)
+    return phi, psi
 
 
 def ka_observe_device(ctx: Ctx, counts_device_ptr: int) -> None:
@@ -401,6 +413,9 @@ class Simulation:
 
     def get_state(self):
         return ka_get_state(self.ctx)
+
+    def four_point(self, smax: int, with_psi: bool = True):
+        return ka_four_point(self.ctx, smax, with_psi)
 
     def set_state(self, n, n0, p, sweep: int, seed: int) -> None:
         ka_set_state(self.ctx, n, n0, p, sweep, seed)
