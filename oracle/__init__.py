@@ -75,6 +75,8 @@ def _load():
         lib.ora_observe.restype = None
         lib.ora_four_point.argtypes = [I, I, I64, u8p, u8p, I64, i64p, i64p]
         lib.ora_four_point.restype = I
+        lib.ora_layered_graph.argtypes = [I, I, I, U64, i32p]
+        lib.ora_layered_graph.restype = I
         for name in ("ora_cubic_tables", "ora_rrg_build", "ora_graph_edges", "ora_graph_classes",
                      "ora_check_schedule", "ora_local_move", "ora_init", "ora_class_step",
                      "ora_sweeps"):
@@ -241,6 +243,14 @@ def four_point(d: int, L: int, st: State, smax: int):
     psi = np.zeros(smax + 1, np.int64)
     _check(_load().ora_four_point(d, L, st.Rs, st.n, st.n0, smax, phi, psi), "four_point")
     return phi, psi
+
+
+def layered_graph(d: int, L: int, M: int, graph_seed: int) -> np.ndarray:
+    """int32 [M L^d, 2d] neighbour rows of the layered random graph (section 5.2)."""
+    N = L ** d
+    nbr = np.zeros(M * N * 2 * d, np.int32)
+    _check(_load().ora_layered_graph(d, L, M, graph_seed, nbr), "layered_graph")
+    return nbr.reshape(M * N, 2 * d)
 
 
 def pack_words(bits: np.ndarray) -> np.ndarray:

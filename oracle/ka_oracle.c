@@ -40,6 +40,7 @@
 /* Counter field c1 tags the stream: bond classes use ids below these. */
 #define ORA_TAG_INIT 0xFFFFFFFFu
 #define ORA_TAG_GRAPH 0xFFFFFFFEu
+#define ORA_TAG_LAYER 0xFFFFFFFDu
 
 /* ------------------------------------------------------------------ */
 /* Philox4x32-10                                                       */
@@ -667,5 +668,66 @@ int ora_four_point(int d, int L, int64_t Rs, const uint8_t *n, const uint8_t *n0
         }
     }
     free(M);
+    return 0;
+}
+
+/* Uniform integer in [0, range) by Lemire's method on the Philox words of
+ * counter (c0, tag, c2, draw), draw = 0, 1, ... until accepted. */
+static uint64_t ora_bounded_at(uint64_t gseed, uint32_t c0, uint32_t tag, uint32_t c2,
+                               uint64_t range)
+{
+    uint32_t draw = 0, o[4];
+    ora_philox_seeded(gseed, c0, tag, c2, draw, o);
+    uint64_t x = (uint64_t)o[0] | ((uint64_t)o[1] << 32);
+    unsigned __int128 prod = (unsigned __int128)x * range;
+    uint64_t low = (uint64_t)prod;
+    if (low < range) {
+        uint64_t threshold = (0 - range) % range;
+        while (low < threshold) {
+            draw++;
+            ora_philox_seeded(gseed, c0, tag, c2, draw, o);
+            x = (uint64_t)o[0] | ((uint64_t)o[1] << 32);
+            prod = (unsigned __int128)x * range;
+            low = (uint64_t)prod;
+        }
+    }
+    return (uint64_t)(prod >> 64);
+}
+
+int ora_layered_graph(int d, int L, int M, uint64_t graph_seed, int32_t *nbr)
+{
+    if (d < 1 || d > 4 || L < 3 || M < 1 || M >= 65536) return ORA_EINVAL;
+    int64_t N = 1;
+    for (int k = 0; k < d; k++) N *= L;
+    const int z = 2 * d;
+    if ((int64_t)M * N * z > 0x7FFFFFFFLL) return ORA_EINVAL;
+    int32_t *perm = (int32_t *)malloc((size_t)M * sizeof(int32_t));
+    if (!perm) return ORA_ENOMEM;
+    for (int64_t i = 0; i < N; i++) {
+        for (int mu = 0; mu < d; mu++) {
+            /* the base bond (i, i + e_mu), periodic */
+            int64_t stride = 1;
+            for (int k = 0; k < mu; k++) stride *= L;
+            const int64_t x = (i / stride) % L;
+            const int64_t j = (x == L - 1) ? i - (int64_t)(L - 1) * stride : i + stride;
+            /* a uniform permutation of the M layers, Fisher-Yates from the top */
+            for (int a = 0; a < M; a++) perm[a] = a;
+            for (int k = M - 1; k >= 1; k--) {
+                const int r = (int)ora_bounded_at(graph_seed, (uint32_t)i, ORA_TAG_LAYER,
+                                                  ((uint32_t)mu << 16) | (uint32_t)k,
+                                                  (uint64_t)(k + 1));
+                const int tmp = perm[k];
+                perm[k] = perm[r];
+                perm[r] = tmp;
+            }
+            /* copy a of i is linked to copy perm[a] of j */
+            for (int a = 0; a < M; a++) {
+                const int64_t u = (int64_t)a * N + i, v = (int64_t)perm[a] * N + j;
+                nbr[u * z + 2 * mu] = (int32_t)v;
+                nbr[v * z + 2 * mu + 1] = (int32_t)u;
+            }
+        }
+    }
+    free(perm);
     return 0;
 }

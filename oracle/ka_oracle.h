@@ -101,6 +101,17 @@ void ora_observe(int64_t N, int64_t Rs, const uint8_t *n, const uint8_t *n0,
 int ora_four_point(int d, int L, int64_t Rs, const uint8_t *n, const uint8_t *n0, int64_t smax,
                    int64_t *phi, int64_t *psi);
 
+/* Layered random graph (section 5.2): M copies of the periodic cubic lattice
+ * of side L in d dimensions (vertex a N + i is site i of copy a); for every
+ * base bond (i, i + e_mu) the M links (copy a of i, copy a of j) are replaced
+ * by (copy a of i, copy pi(a) of j), pi a uniform permutation of the copies
+ * drawn independently per bond: Fisher-Yates from the top, step k drawing a
+ * uniform integer in [0, k] by Lemire's method on the Philox words of counter
+ * (i, 0xFFFFFFFD, mu << 16 | k, draw) keyed by the graph seed.  nbr[M N][2d]:
+ * entry 2 mu is the neighbour across the up bond along mu, 2 mu + 1 across
+ * the down bond.  Needs 1 <= d <= 4, L >= 3, 1 <= M < 65536. */
+int ora_layered_graph(int d, int L, int M, uint64_t graph_seed, int32_t *nbr);
+
 #ifdef __cplusplus
 }
 #endif
