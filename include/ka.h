@@ -197,6 +197,21 @@ ka_status ka_build_topology(const ka_params *params, int64_t *nclass, int64_t *n
                             int32_t *nbr,
                       int64_t *class_off, int32_t *bu, int32_t *bv, int64_t *bid);
 
+/* Host only: neighbour rows nbr[M L^d][2d] (int32, caller-allocated) of the
+ * layered random graph of section 5.2, to be run as a KA_GRAPH topology with
+ * N = M L^d and z = 2d.  M copies of the periodic cubic lattice of side L in
+ * d dimensions, vertex a L^d + i being site i of copy a; for every base bond
+ * (i, i + e_mu) the M links between the copies of i and those of j = i + e_mu
+ * are rewired by a uniform permutation pi of the copies, independent per
+ * bond: copy a of i is linked to copy pi(a) of j.  pi is drawn by
+ * Fisher-Yates from the top, step k taking a uniform integer in [0, k] by
+ * Lemire's method on the low 64 bits of Philox4x32-10 at counter
+ * (i, 0xFFFFFFFD, mu << 16 | k, draw), key = graph_seed, draw = 0, 1, ...
+ * until accepted.  Entry 2 mu of a row is the neighbour across the up bond
+ * along mu, entry 2 mu + 1 across the down bond.  M = 1 gives the lattice.
+ * KA_EINVAL unless 1 <= d <= 4, L >= 3, 1 <= M < 65536, M L^d 2d < 2^31. */
+ka_status ka_layered_graph(int32_t d, int32_t L, int32_t M, uint64_t graph_seed, int32_t *nbr);
+
 /* Kernel timing for roofline reports.  When enabled, ka_sweep brackets
  * every sweep-kernel launch with CUDA events on the context stream;
  * ka_profile_read synchronises and returns the summed kernel time and the

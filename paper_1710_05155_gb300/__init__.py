@@ -81,6 +81,7 @@ _SIGS = {
     "ka_batch_add": (C.c_int, [C.c_void_p, _P(ka_params), _P(ka_job_spec), _P(C.c_int64)]),
     "ka_job_bytes": (C.c_int, [_P(ka_params), _P(ka_job_spec), _P(C.c_size_t)]),
     "ka_four_point": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "ka_layered_graph": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_void_p]),
     "ka_batch_adopt": (C.c_int, [C.c_void_p, C.c_void_p, _P(ka_job_spec), _P(C.c_int64)]),
     "ka_batch_step": (C.c_int, [C.c_void_p, C.c_int64, _P(C.c_int64)]),
     "ka_batch_autotune": (C.c_int, [C.c_void_p, _P(C.c_int64)]),
@@ -168,6 +169,14 @@ def ka_job_bytes(params: ka_params, sweeps: int, observe_every: int) -> int:
     spec = ka_job_spec(sweeps, observe_every, 0, 0.0)
     _check(load().ka_job_bytes(C.byref(params), C.byref(spec), C.byref(out)), "ka_job_bytes")
     return out.value
+
+
+def ka_layered_graph(d: int, L: int, M: int, graph_seed: int) -> np.ndarray:
+    """int32 [M L^d, 2d] neighbour rows of the layered random graph (section 5.2):
+    pass them as KA_GRAPH with N = M L^d, z = 2d."""
+    nbr = np.zeros((M * L ** d, 2 * d), np.int32)
+    _check(load().ka_layered_graph(d, L, M, graph_seed, _ptr(nbr)), "ka_layered_graph")
+    return nbr
 
 
 def ka_create(params: ka_params, keep=()) -> Ctx:

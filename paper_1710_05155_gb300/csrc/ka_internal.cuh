@@ -21,6 +21,7 @@ namespace ka {
 
 constexpr uint32_t kTagInit = 0xFFFFFFFFu;   // counter word c1 of the initial-state keys
 constexpr uint32_t kTagGraph = 0xFFFFFFFEu;  // counter word c1 of the graph shuffle
+constexpr uint32_t kTagLayer = 0xFFFFFFFDu;  // counter word c1 of the layer permutations
 constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
 constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
@@ -78,6 +79,8 @@ struct Topology {
 std::string build_cubic_tables(int d, int L, Topology& t);
 std::string build_rrg(int64_t N, int z, uint64_t graph_seed, Topology& t);
 std::string build_graph(int64_t N, int z, const int32_t* nbr, Topology& t);
+// Neighbour rows [M L^d][2d] of the layered random graph (section 5.2).
+std::string build_layered(int d, int L, int M, uint64_t graph_seed, int32_t* nbr);
 
 // --------------------------------------------------------------------------
 // Kernel launchers

@@ -13,6 +13,12 @@
 //    passed them, so a bad attempt is abandoned early; the accepted graph is
 //    the same either way.  Attempts run on several host threads; the graph
 //    kept is always that of the lowest-numbered simple attempt.
+//  * Layered random graph (section 5.2): M copies of the periodic cubic
+//    lattice; for every base bond (i, i + e_mu) the M links between the
+//    copies of i and of j = i + e_mu are rewired by a uniform permutation of
+//    the copies (Fisher-Yates from the top; step k draws a uniform integer in
+//    [0, k] by Lemire's method on counter (i, 0xFFFFFFFD, mu << 16 | k,
+//    draw)), independently per bond.  Vertex a N + i is site i of copy a.
 //  * Bond classes of a graph: greedy strong edge colouring of the edges
 //    (u < v, lexicographic ids) in id order; classes in ascending colour.
 #include <algorithm>
@@ -287,3 +293,75 @@ std::string build_graph(int64_t N, int z, const int32_t* nbr, Topology& t) {
 }
 
 }  // namespace ka
+
+namespace ka {
+
+std::string build_layered(int d, int L, int M, uint64_t graph_seed, int32_t* nbr) {
+  if (d < 1 || d > 4 || L < 3 || M < 1 || M >= 65536)
+    return "layered graph needs 1 <= d <= 4, L >= 3, 1 <= M < 65536";
+  int64_t N = 1;
+  for (int k = 0; k < d; ++k) N *= L;
+  const int z = 2 * d;
+  if ((int64_t)M * N * z > 0x7FFFFFFFLL) return "layered graph: M L^d 2d must stay below 2^31";
+  const RoundKeys rk = round_keys(graph_seed);
+  // uniform integer in [0, range) from the words of counter (c0, tag, c2, draw)
+  auto bounded = [&rk](uint32_t c0, uint32_t c2, uint64_t range) -> uint64_t {
+    uint32_t draw = 0;
+    uint64_t x = lo64(philox(make_uint4(c0, kTagLayer, c2, draw), rk));
+    unsigned __int128 prod = (unsigned __int128)x * range;
+    uint64_t low = (uint64_t)prod;
+    if (low < range) {
+      const uint64_t floor = (0 - range) % range;
+      while (low < floor) {
+        ++draw;
+        x = lo64(philox(make_uint4(c0, kTagLayer, c2, draw), rk));
+        prod = (unsigned __int128)x * range;
+        low = (uint64_t)prod;
+      }
+    }
+    return (uint64_t)(prod >> 64);
+  };
+  // bonds are independent and each writes its own slots (the up slot along
+  // mu of the copies of i, the down slot of the copies of j): split the
+  // base sites over threads
+  auto work = [&](int64_t i0, int64_t i1) {
+    std::vector<int32_t> perm(M);
+    for (int64_t i = i0; i < i1; ++i) {
+      int64_t stride = 1;
+      for (int mu = 0; mu < d; ++mu, stride *= L) {
+        const int64_t x = (i / stride) % L;
+        const int64_t j = (x == L - 1) ? i - (int64_t)(L - 1) * stride : i + stride;
+        for (int a = 0; a < M; ++a) perm[a] = a;
+        for (int k = M - 1; k >= 1; --k) {
+          const int r = (int)bounded((uint32_t)i, ((uint32_t)mu << 16) | (uint32_t)k,
+                                     (uint64_t)(k + 1));
+          std::swap(perm[k], perm[r]);
+        }
+        for (int a = 0; a < M; ++a) {
+          const int64_t u = (int64_t)a * N + i, v = (int64_t)perm[a] * N + j;
+          nbr[u * z + 2 * mu] = (int32_t)v;
+          nbr[v * z + 2 * mu + 1] = (int32_t)u;
+        }
+      }
+    }
+  };
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int64_t nt = std::min<int64_t>(std::min<unsigned>(hw, 16u),
+                                       std::max<int64_t>(1, N * M / 65536));
+  if (nt <= 1) {
+    work(0, N);
+  } else {
+    std::vector<std::thread> pool;
+    for (int64_t t = 0; t < nt; ++t) pool.emplace_back(work, N * t / nt, N * (t + 1) / nt);
+    for (auto& th : pool) th.join();
+  }
+  return "";
+}
+
+}  // namespace ka
+
+extern "C" ka_status ka_layered_graph(int32_t d, int32_t L, int32_t M, uint64_t graph_seed,
+                                      int32_t* nbr) {
+  if (!nbr) return KA_EINVAL;
+  return ka::build_layered(d, L, M, graph_seed, nbr).empty() ? KA_OK : KA_EINVAL;
+}

@@ -131,3 +131,16 @@ def test_caller_graph_validation(bad):
     p, keep = K.make_params(topo=K.KA_GRAPH, N=N, z=z, m=1, nbr=ring)
     with pytest.raises(K.KaError):
         K.ka_build_topology(p)
+
+
+@pytest.mark.parametrize("d,L,M,seed", [(3, 4, 2, 1), (3, 8, 16, 7), (2, 8, 8, 3), (1, 16, 3, 2),
+                                        (4, 3, 2, 5), (3, 32, 4, 9)])  # the last one is threaded
+def test_layered_graph_matches_oracle(d, L, M, seed):
+    assert (K.ka_layered_graph(d, L, M, seed) == O.layered_graph(d, L, M, seed)).all()
+
+
+@pytest.mark.parametrize("d,L,M", [(0, 4, 2), (5, 4, 2), (3, 2, 2), (3, 4, 0), (3, 4, 65536)])
+def test_layered_graph_rejects(d, L, M):
+    with pytest.raises(K.KaError) as e:
+        K.ka_layered_graph(d, L, M, 1)
+    assert e.value.status == K.KA_EINVAL

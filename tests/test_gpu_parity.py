@@ -25,6 +25,8 @@ import paper_1710_05155_gb300 as K  # noqa: E402
 def _oracle_topo(kw):
     if kw.get("topo", K.KA_CUBIC) == K.KA_CUBIC:
         return O.cubic(kw["d"], kw["L"])
+    if kw["topo"] == K.KA_GRAPH:
+        return O.graph(kw["N"], kw["z"], np.ascontiguousarray(kw["nbr"], np.int32).ravel())
     return O.rrg(kw["N"], kw["z"], kw.get("graph_seed", 1))
 
 
@@ -106,6 +108,14 @@ RRG = [
 @pytest.mark.parametrize("kw", RRG, ids=lambda k: f"N{k['N']}z{k['z']}m{k['m']}R{k['replicas']}")
 def test_rrg_every_sweep(kw):
     _run_case(dict(topo=K.KA_RRG, graph_seed=3, **kw), seed=11, rho=0.7, sweeps=4)
+
+
+@pytest.mark.parametrize("d,L,M,m,R", [(3, 4, 4, 3, 64), (3, 6, 2, 2, 128), (2, 8, 8, 1, 256)])
+def test_layered_graph_every_sweep(d, L, M, m, R):
+    # section 5.2 graph from the oracle's generator, run as a caller-supplied graph
+    nbr = O.layered_graph(d, L, M, 3)
+    _run_case(dict(topo=K.KA_GRAPH, N=M * L ** d, z=2 * d, m=m, replicas=R, nbr=nbr),
+              seed=13, rho=0.7, sweeps=4)
 
 
 def test_rrg_tables_match_oracle():
