@@ -77,6 +77,8 @@ def _load():
         lib.ora_four_point.restype = I
         lib.ora_layered_graph.argtypes = [I, I, I, U64, i32p]
         lib.ora_layered_graph.restype = I
+        lib.ora_sequential_sweeps.argtypes = [I64, I, i32p, I, U64, I64, I64, I64, I64, u8p, u8p]
+        lib.ora_sequential_sweeps.restype = I
         for name in ("ora_cubic_tables", "ora_rrg_build", "ora_graph_edges", "ora_graph_classes",
                      "ora_check_schedule", "ora_local_move", "ora_init", "ora_class_step",
                      "ora_sweeps"):
@@ -243,6 +245,14 @@ def four_point(d: int, L: int, st: State, smax: int):
     psi = np.zeros(smax + 1, np.int64)
     _check(_load().ora_four_point(d, L, st.Rs, st.n, st.n0, smax, phi, psi), "four_point")
     return phi, psi
+
+
+def sequential_sweeps(topo: Topology, m: int, st: State, seed: int, nsweeps: int) -> None:
+    """Random-sequential sweeps (one random bond per attempt, shared by the 64
+    replicas of a word; N attempts per sweep) from sweep st.t; advances st.t."""
+    _check(_load().ora_sequential_sweeps(topo.N, topo.z, topo.nbr, m, seed, st.r0, st.Rs, st.t,
+                                         nsweeps, st.n, st.p), "sequential_sweeps")
+    st.t += nsweeps
 
 
 def layered_graph(d: int, L: int, M: int, graph_seed: int) -> np.ndarray:

@@ -41,6 +41,7 @@
 #define ORA_TAG_INIT 0xFFFFFFFFu
 #define ORA_TAG_GRAPH 0xFFFFFFFEu
 #define ORA_TAG_LAYER 0xFFFFFFFDu
+#define ORA_TAG_SEQUENTIAL 0xFFFFFFFCu
 
 /* ------------------------------------------------------------------ */
 /* Philox4x32-10                                                       */
@@ -730,4 +731,69 @@ int ora_layered_graph(int d, int L, int M, uint64_t graph_seed, int32_t *nbr)
     }
     free(perm);
     return 0;
+}
+
+/* Attempt k of sweep t of word w in the random-sequential mode: a uniform
+ * integer in [0, N z) by Lemire's method on the low 64 bits of the Philox
+ * block at counter (t, 0xFFFFFFFC - draw, k, w), draw = 0, 1, ... */
+static uint64_t ora_sequential_draw(uint64_t seed, uint32_t t, uint32_t k, uint32_t w,
+                                    uint64_t range)
+{
+    uint32_t draw = 0, o[4];
+    ora_philox_seeded(seed, t, ORA_TAG_SEQUENTIAL - draw, k, w, o);
+    uint64_t x = (uint64_t)o[0] | ((uint64_t)o[1] << 32);
+    unsigned __int128 prod = (unsigned __int128)x * range;
+    uint64_t low = (uint64_t)prod;
+    if (low < range) {
+        uint64_t threshold = (0 - range) % range;
+        while (low < threshold) {
+            draw++;
+            ora_philox_seeded(seed, t, ORA_TAG_SEQUENTIAL - draw, k, w, o);
+            x = (uint64_t)o[0] | ((uint64_t)o[1] << 32);
+            prod = (unsigned __int128)x * range;
+            low = (uint64_t)prod;
+        }
+    }
+    return (uint64_t)(prod >> 64);
+}
+
+int ora_sequential_sweeps(int64_t N, int z, const int32_t *nbr, int m, uint64_t seed, int64_t r0,
+                          int64_t Rs, int64_t t0, int64_t nsweeps, uint8_t *n, uint8_t *p)
+{
+    if (N < 1 || z < 1 || m < 0 || r0 < 0 || Rs < 0 || (r0 % 64) != 0 || (Rs % 64) != 0 ||
+        N * z > 0xFFFFFFFFLL)
+        return ORA_EINVAL;
+    for (int64_t w = 0; w < Rs / 64; w++) {
+        const int64_t word = r0 / 64 + w;
+        for (int64_t t = t0; t < t0 + nsweeps; t++) {
+            for (int64_t k = 0; k < N; k++) {
+                /* the bond: site i and its neighbour in slot s, shared by the
+                 * 64 replicas of the word (section 3.2) */
+                const uint64_t r = ora_sequential_draw(seed, (uint32_t)t, (uint32_t)k,
+                                                       (uint32_t)word, (uint64_t)(N * z));
+                const int64_t i = (int64_t)(r / (uint64_t)z);
+                const int64_t j = nbr[i * z + (int64_t)(r % (uint64_t)z)];
+                for (int64_t b = 0; b < 64; b++) {
+                    const int64_t rr = w * 64 + b;
+                    int ni = n[i * Rs + rr], nj = n[j * Rs + rr];
+                    int ci = 0, cj = 0;
+                    for (int s = 0; s < z; s++) {
+                        int64_t x = nbr[i * z + s];
+                        if (x != j) ci += n[x * Rs + rr];
+                        x = nbr[j * z + s];
+                        if (x != i) cj += n[x * Rs + rr];
+                    }
+                    int ni2, nj2;
+                    ora_rule(m, ni, nj, ci, cj, 1, &ni2, &nj2);
+                    if (ni2 != ni) {
+                        n[i * Rs + rr] = (uint8_t)ni2;
+                        n[j * Rs + rr] = (uint8_t)nj2;
+                        p[i * Rs + rr] = 0;
+                        p[j * Rs + rr] = 0;
+                    }
+                }
+            }
+        }
+    }
+    return ORA_OK;
 }

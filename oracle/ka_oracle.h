@@ -112,6 +112,17 @@ int ora_four_point(int d, int L, int64_t Rs, const uint8_t *n, const uint8_t *n0
  * the down bond.  Needs 1 <= d <= 4, L >= 3, 1 <= M < 65536. */
 int ora_layered_graph(int d, int L, int M, uint64_t graph_seed, int32_t *nbr);
 
+/* Random-sequential sweeps (section 3.2 with the time unit of section 2.1):
+ * per word of 64 replicas and per sweep t, N attempts k = 0 .. N-1; attempt k
+ * draws r uniform in [0, N z) (Lemire's method on the low 64 bits of the
+ * Philox block at counter (t, 0xFFFFFFFC - draw, k, word), key = seed,
+ * draw = 0, 1, ...), takes site i = r / z and its neighbour j in slot r mod z,
+ * and exchanges n_i and n_j in every replica of the word where the rule
+ * allows it (no gate; p cleared on both sites).  All replicas of a word share
+ * the bond sequence.  Replicas r0 .. r0+Rs-1, r0 and Rs multiples of 64. */
+int ora_sequential_sweeps(int64_t N, int z, const int32_t *nbr, int m, uint64_t seed, int64_t r0,
+                          int64_t Rs, int64_t t0, int64_t nsweeps, uint8_t *n, uint8_t *p);
+
 #ifdef __cplusplus
 }
 #endif
