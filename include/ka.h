@@ -142,6 +142,21 @@ ka_status ka_init(ka_ctx *ctx, uint64_t seed, double rho);
  * counter must stay below 2^32 (it is a Philox counter word). */
 ka_status ka_sweep(ka_ctx *ctx, int64_t n);
 
+/* n sweeps of the paper's random-sequential schedule (section 3.2) instead
+ * of the class schedule: each attempt picks one bond, shared by the 64
+ * replicas of a word, and exchanges the two sites in every replica where the
+ * rule of section 2.1 allows it (no gate); N attempts make a sweep.  Attempt
+ * k of sweep t of word w draws r uniform in [0, N z) by Lemire's method on
+ * the low 64 bits of Philox4x32-10 at counter (t, 0xFFFFFFFC - draw, k, w),
+ * key = the dynamics seed, draw = 0, 1, ... until accepted, and takes site
+ * i = r / z and its neighbour in slot r mod z (on cubic lattices slot 2 mu is
+ * the up and 2 mu + 1 the down neighbour along mu; on graphs the slots are
+ * the neighbour row in ascending order, as ka_graph_tables returns it).  One warp per word runs
+ * the chain, in shared memory when the lattice has at most 10240 sites; it is
+ * a reference schedule, not a fast one.  Advances the sweep counter; no
+ * synchronisation.  KA_ESTATE before init, KA_EINVAL if N z >= 2^32. */
+ka_status ka_sweep_sequential(ka_ctx *ctx, int64_t n);
+
 /* Observables of the current state into host int64 counts[R][4]; writes the
  * sweep counter to *sweep_out (may be NULL).  Synchronises the stream. */
 ka_status ka_observe(ka_ctx *ctx, int64_t *sweep_out, int64_t *counts);

@@ -82,6 +82,7 @@ _SIGS = {
     "ka_job_bytes": (C.c_int, [_P(ka_params), _P(ka_job_spec), _P(C.c_size_t)]),
     "ka_four_point": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "ka_layered_graph": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_void_p]),
+    "ka_sweep_sequential": (C.c_int, [C.c_void_p, C.c_int64]),
     "ka_batch_adopt": (C.c_int, [C.c_void_p, C.c_void_p, _P(ka_job_spec), _P(C.c_int64)]),
     "ka_batch_step": (C.c_int, [C.c_void_p, C.c_int64, _P(C.c_int64)]),
     "ka_batch_autotune": (C.c_int, [C.c_void_p, _P(C.c_int64)]),
@@ -198,6 +199,12 @@ def ka_init(ctx: Ctx, seed: int, rho: float) -> None:
 
 def ka_sweep(ctx: Ctx, n: int) -> None:
     _check(load().ka_sweep(ctx.handle, n), "ka_sweep", ctx)
+
+
+def ka_sweep_sequential(ctx: Ctx, n: int) -> None:
+    """n sweeps of the random-sequential schedule (one bond per attempt, shared by the
+    replicas of a word; N attempts per sweep)."""
+    _check(load().ka_sweep_sequential(ctx.handle, n), "ka_sweep_sequential", ctx)
 
 
 def ka_info(ctx: Ctx) -> dict:
@@ -416,6 +423,9 @@ class Simulation:
 
     def sweep(self, n: int) -> None:
         ka_sweep(self.ctx, n)
+
+    def sweep_sequential(self, n: int) -> None:
+        ka_sweep_sequential(self.ctx, n)
 
     def observe(self):
         return ka_observe(self.ctx)

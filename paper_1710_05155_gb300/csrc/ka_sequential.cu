@@ -1,0 +1,257 @@
+// ka_sequential.cu -- the random-sequential schedule of section 3.2.
+//
+// The paper's own update: each step picks one bond at random, shared by all
+// replicas packed in a word, and exchanges the two sites in every replica
+// where the rule of section 2.1 allows it (no per-replica gate).  N attempts
+// make a sweep (the time unit of section 2.1).  Attempt k of sweep t of word
+// w draws r uniform in [0, N z) by Lemire's method on the low 64 bits of the
+// Philox block at counter (t, 0xFFFFFFFC - draw, k, w), key = seed, and takes
+// site i = r / z and its neighbour in slot r mod z (slots 2 mu and 2 mu + 1
+// are the up and down neighbours along mu on a cubic lattice; on a graph the
+// slots follow the neighbour row, kept in ascending order).
+//
+// The attempts of one word form a chain, so one warp runs one word: its 32
+// lanes draw 32 attempts at a time (the draws do not depend on the state),
+// then lane 0 applies them in order.  The word's n and p planes sit in shared
+// memory when they fit, else the chain works on global memory.
+#include <algorithm>
+#include <string>
+
+#include "ka_ctx.cuh"
+
+namespace ka {
+namespace {
+
+constexpr uint32_t kTagSequential = 0xFFFFFFFCu;
+constexpr int kSmemWords = 20480;  // n and p of up to 10240 sites in shared memory
+
+struct SeqArgs {
+  uint64_t* n;
+  uint64_t* p;
+  const int32_t* nbr;  // [N][z], or null: periodic cubic lattice from coordinates
+  int64_t N;
+  int z, d, L, V;
+  size_t plane_elems;
+  uint32_t t0;
+  int nsweeps;
+  RoundKeys rk;
+};
+
+__device__ __forceinline__ void add3(uint64_t& c2, uint64_t& c1, uint64_t& c0, uint64_t x) {
+  const uint64_t k0 = c0 & x;
+  c0 ^= x;
+  const uint64_t k1 = c1 & k0;
+  c1 ^= k0;
+  c2 |= k1;
+}
+
+template <int T>
+__device__ __forceinline__ uint64_t le3(uint64_t b2, uint64_t b1, uint64_t b0) {
+  if constexpr (T < 0) {
+    return 0ull;
+  } else if constexpr (T >= 7) {
+    return ~0ull;
+  } else {
+    const uint64_t g0 = (T & 1) ? 0ull : b0;
+    const uint64_t g1 = (T & 2) ? (b1 & g0) : (b1 | g0);
+    const uint64_t g2 = (T & 4) ? (b2 & g1) : (b2 | g1);
+    return ~g2;
+  }
+}
+
+// the bond draw of attempt k: r uniform in [0, range)
+__device__ __forceinline__ uint64_t draw_bond(const RoundKeys& rk, uint32_t t, uint32_t k,
+                                              uint32_t w, uint64_t range) {
+  uint32_t draw = 0;
+  uint64_t x = lo64(philox(make_uint4(t, kTagSequential, k, w), rk));
+  uint64_t low = x * range;
+  if (low < range) {
+    const uint64_t threshold = (0ull - range) % range;
+    while (low < threshold) {
+      ++draw;
+      x = lo64(philox(make_uint4(t, kTagSequential - draw, k, w), rk));
+      low = x * range;
+    }
+  }
+  return __umul64hi(x, range);
+}
+
+// the 2d neighbours of site i of a periodic cubic lattice, slot 2 mu up and
+// 2 mu + 1 down along mu (32-bit arithmetic: N z < 2^32)
+__device__ __forceinline__ void cubic_neighbours(const SeqArgs& a, uint32_t i, uint32_t (&out)[8]) {
+  uint32_t rest = i, stride = 1;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    if (mu >= a.d) break;
+    const uint32_t L = (uint32_t)a.L, q = rest / L, x = rest - q * L;
+    rest = q;
+    out[2 * mu] = (x == L - 1) ? i - (L - 1) * stride : i + stride;
+    out[2 * mu + 1] = (x == 0) ? i + (L - 1) * stride : i - stride;
+    stride *= L;
+  }
+}
+
+// the z neighbours of site i
+__device__ __forceinline__ void neighbours(const SeqArgs& a, uint32_t i, uint32_t (&out)[8]) {
+  if (a.nbr) {
+#pragma unroll
+    for (int s = 0; s < 8; ++s)
+      if (s < a.z) out[s] = (uint32_t)a.nbr[(int64_t)i * a.z + s];
+  } else {
+    cubic_neighbours(a, i, out);
+  }
+}
+
+// one warp per word; n and p of the word at stride `st` (V in global memory,
+// 1 in shared memory)
+template <int M, bool SMEM>
+__global__ void __launch_bounds__(32) k_sequential(const __grid_constant__ SeqArgs a) {
+  extern __shared__ uint64_t sm[];
+  const int lane = threadIdx.x;
+  const uint32_t w = blockIdx.x;  // word index
+  const int q = (int)(w / (uint32_t)a.V), h = (int)(w % (uint32_t)a.V);
+  uint64_t* gn = a.n + (size_t)q * a.plane_elems + h;
+  uint64_t* gp = a.p + (size_t)q * a.plane_elems + h;
+  uint64_t* n = gn;
+  uint64_t* p = gp;
+  int64_t st = a.V;
+  if constexpr (SMEM) {
+    for (int64_t i = lane; i < a.N; i += 32) {
+      sm[i] = gn[i * a.V];
+      sm[a.N + i] = gp[i * a.V];
+    }
+    __syncwarp();
+    n = sm;
+    p = sm + a.N;
+    st = 1;
+  }
+  const uint64_t range = (uint64_t)a.N * (uint64_t)a.z;
+  for (int s = 0; s < a.nsweeps; ++s) {
+    const uint32_t t = a.t0 + (uint32_t)s;
+    for (int64_t k0 = 0; k0 < a.N; k0 += 32) {
+      const int64_t k = k0 + lane;
+      const uint64_t r = (k < a.N) ? draw_bond(a.rk, t, (uint32_t)k, w, range) : 0ull;
+      const int cnt = (a.N - k0) < 32 ? (int)(a.N - k0) : 32;
+      for (int l = 0; l < cnt; ++l) {
+        const uint64_t rl = __shfl_sync(0xffffffffu, r, l);
+        if (lane == 0) {
+          const uint32_t i = (uint32_t)(rl / (uint64_t)a.z);
+          uint32_t ni_[8], nj_[8];
+          neighbours(a, i, ni_);
+          const int sel = (int)(rl % (uint64_t)a.z);
+          uint32_t j = 0;
+#pragma unroll
+          for (int s2 = 0; s2 < 8; ++s2)
+            if (s2 == sel) j = ni_[s2];
+          neighbours(a, j, nj_);
+          const uint64_t vi = n[(int64_t)i * st], vj = n[(int64_t)j * st];
+          uint64_t ci2 = 0, ci1 = 0, ci0 = 0, cj2 = 0, cj1 = 0, cj0 = 0;
+#pragma unroll
+          for (int slot = 0; slot < 8; ++slot) {
+            if (slot >= a.z) break;
+            if (ni_[slot] != j) add3(ci2, ci1, ci0, n[(int64_t)ni_[slot] * st]);
+            if (nj_[slot] != i) add3(cj2, cj1, cj0, n[(int64_t)nj_[slot] * st]);
+          }
+          // at most m occupied among the other neighbours of i and of j
+          const uint64_t ok = le3<M>(ci2, ci1, ci0) & le3<M>(cj2, cj1, cj0);
+          const uint64_t sw = (vi ^ vj) & ok;
+          if (sw) {
+            n[(int64_t)i * st] = vi ^ sw;
+            n[(int64_t)j * st] = vj ^ sw;
+            p[(int64_t)i * st] &= ~sw;
+            p[(int64_t)j * st] &= ~sw;
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  if constexpr (SMEM) {
+    __syncwarp();
+    for (int64_t i = lane; i < a.N; i += 32) {
+      gn[i * a.V] = sm[i];
+      gp[i * a.V] = sm[a.N + i];
+    }
+  }
+}
+
+template <bool SMEM>
+cudaError_t launch_m(const SeqArgs& a, int m, unsigned words, size_t smem, cudaStream_t st) {
+  switch (m < 7 ? m : 7) {
+#define KA_CASE(MM)                                                                        \
+  case MM: {                                                                               \
+    auto kern = k_sequential<MM, SMEM>;                                                    \
+    if (smem > 48 * 1024) {                                                                \
+      const cudaError_t e =                                                                \
+          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+      if (e != cudaSuccess) return e;                                                      \
+    }                                                                                      \
+    kern<<<words, 32, smem, st>>>(a);                                                      \
+    return cudaGetLastError();                                                             \
+  }
+    KA_CASE(0)
+    KA_CASE(1)
+    KA_CASE(2)
+    KA_CASE(3)
+    KA_CASE(4)
+    KA_CASE(5)
+    KA_CASE(6)
+    KA_CASE(7)
+#undef KA_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+}  // namespace ka
+
+extern "C" ka_status ka_sweep_sequential(ka_ctx* c, int64_t nsweeps) {
+  using namespace ka;
+  if (!c || nsweeps < 0) return KA_EINVAL;
+  if (!c->initialized) {
+    c->err = "sequential sweep before init or set_state";
+    return KA_ESTATE;
+  }
+  if (c->sweep + nsweeps > ((int64_t)1 << 32)) {
+    c->err = "sweep counter would pass 2^32";
+    return KA_EINVAL;
+  }
+  if ((uint64_t)c->N * (uint64_t)c->z > 0xFFFFFFFFull) {
+    c->err = "N z must stay below 2^32";
+    return KA_EINVAL;
+  }
+  if (nsweeps == 0) return KA_OK;
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess || prev == c->device) prev = -1;
+  if (prev >= 0) cudaSetDevice(c->device);
+  SeqArgs a{};
+  a.n = c->pl.n;
+  a.p = c->pl.p;
+  a.nbr = c->pencil ? nullptr : c->g.nbr;
+  a.N = c->N;
+  a.z = c->z;
+  a.d = c->d;
+  a.L = c->L;
+  a.V = c->pl.V;
+  a.plane_elems = c->pl.plane_elems();
+  a.rk = c->rk;
+  const unsigned words = (unsigned)(c->R / 64);
+  const bool smem = 2 * c->N <= kSmemWords;
+  // launches of at most about 2^20 attempts each
+  const int64_t chunk = std::max<int64_t>(1, ((int64_t)1 << 20) / c->N);
+  cudaError_t e = cudaSuccess;
+  for (int64_t done = 0; done < nsweeps && !e; done += chunk) {
+    a.t0 = (uint32_t)(c->sweep + done);
+    a.nsweeps = (int)std::min<int64_t>(chunk, nsweeps - done);
+    e = smem ? launch_m<true>(a, c->m, words, (size_t)2 * c->N * sizeof(uint64_t), c->stream)
+             : launch_m<false>(a, c->m, words, 0, c->stream);
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  if (e) {
+    c->err = std::string("sequential sweep: ") + cudaGetErrorString(e);
+    return KA_ECUDA;
+  }
+  c->sweep += nsweeps;
+  return KA_OK;
+}
