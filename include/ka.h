@@ -249,7 +249,9 @@ ka_status ka_destroy(ka_ctx *ctx);
  * per plane, m).  Each job's result is bit-identical to running it alone:
  * the random streams are keyed by the job's seed, sweep, class and site,
  * never by its position in the batch.  The paper has no batching; this is
- * the serving layer around its method.
+ * the serving layer around its method.  A batch is not thread-safe: call its
+ * functions from one host thread at a time (contexts for ka_batch_adopt may
+ * be created and initialised on other threads).
  * ------------------------------------------------------------------------ */
 typedef struct ka_batch ka_batch;
 

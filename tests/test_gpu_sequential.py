@@ -100,3 +100,20 @@ def test_sequential_before_init():
         sim.sweep_sequential(1)
     assert e.value.status == K.KA_ESTATE
     sim.close()
+
+
+def test_command_line_runner():
+    # the runner prints one JSON line per observation and a timing line
+    import json
+    import subprocess
+    import sys
+
+    out = subprocess.run([sys.executable, "-m", "paper_1710_05155_gb300.cli", "--topo", "cubic",
+                          "--d", "3", "--L", "16", "--m", "3", "--replicas", "64", "--rho", "0.7",
+                          "--sweeps", "20", "--every", "10"],
+                         capture_output=True, text=True, check=True).stdout.strip().splitlines()
+    rows = [json.loads(x) for x in out]
+    assert [r["sweep"] for r in rows[:-1]] == [0, 10, 20]
+    assert rows[0]["C"] == pytest.approx(1.0) and rows[0]["phi"] == pytest.approx(1.0)
+    assert rows[0]["chi4"] == pytest.approx(0.0, abs=1e-9)
+    assert rows[-1]["sweeps"] == 20 and rows[-1]["site_replica_moves_per_s"] > 0
