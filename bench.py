@@ -310,7 +310,13 @@ def run_native(args, rank: int, world: int) -> None:
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_cubic_group", "peak_kind": peak_kind,
                          "avg_launch_us": 1000.0 * avg_launch_ms,
-                         "bytes_per_launch": bytes_per_launch},
+                         "bytes_per_launch": bytes_per_launch,
+                         # the DRAM bytes the kernel really moves per launch (the committed
+                         # ncu capture) over the same live launch time
+                         "dram_achieved": (traffic / (avg_launch_ms / 1000.0) / 1e9
+                                           if traffic else None),
+                         "dram_frac": (traffic / (avg_launch_ms / 1000.0) / 1e9 / peak
+                                       if traffic else None)},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
