@@ -292,6 +292,7 @@ ka_status ka_create_in(const ka_params* params, void* device_buffer, size_t byte
 }
 
 ka_status ka_init(ka_ctx* c, uint64_t seed, double rho) {
+  ka::NvtxRange nvtx_range("ka_init");
   if (!c) return KA_EINVAL;
   if (!(rho >= 0.0 && rho <= 1.0)) return fail(c, KA_EINVAL, "rho must be in [0, 1]");
   DeviceGuard dg(c->device);
@@ -307,6 +308,7 @@ ka_status ka_init(ka_ctx* c, uint64_t seed, double rho) {
 }
 
 ka_status ka_sweep(ka_ctx* c, int64_t n) {
+  ka::NvtxRange nvtx_range("ka_sweep");
   if (!c || n < 0) return c ? fail(c, KA_EINVAL, "n must be >= 0") : KA_EINVAL;
   if (!c->initialized) return fail(c, KA_ESTATE, "sweep before init or set_state");
   if (c->sweep + n > ((int64_t)1 << 32)) return fail(c, KA_EINVAL, "sweep counter would pass 2^32");
@@ -352,6 +354,7 @@ ka_status ka_sweep(ka_ctx* c, int64_t n) {
 }
 
 ka_status ka_observe_device(ka_ctx* c, int64_t* counts_device) {
+  ka::NvtxRange nvtx_range("ka_observe");
   if (!c || !counts_device) return KA_EINVAL;
   if (!c->initialized) return fail(c, KA_ESTATE, "observe before init or set_state");
   DeviceGuard dg(c->device);
@@ -361,6 +364,7 @@ ka_status ka_observe_device(ka_ctx* c, int64_t* counts_device) {
 }
 
 ka_status ka_observe(ka_ctx* c, int64_t* sweep_out, int64_t* counts) {
+  ka::NvtxRange nvtx_range("ka_observe");
   if (!c || !counts) return KA_EINVAL;
   if (!c->initialized) return fail(c, KA_ESTATE, "observe before init or set_state");
   DeviceGuard dg(c->device);
@@ -374,6 +378,7 @@ ka_status ka_observe(ka_ctx* c, int64_t* sweep_out, int64_t* counts) {
 }
 
 ka_status ka_get_state(ka_ctx* c, uint64_t* n, uint64_t* n0, uint64_t* p) {
+  ka::NvtxRange nvtx_range("ka_get_state");
   if (!c) return KA_EINVAL;
   DeviceGuard dg(c->device);
   const size_t bytes = (size_t)c->pl.P * c->pl.plane_elems() * sizeof(uint64_t);
@@ -398,6 +403,7 @@ ka_status ka_get_state(ka_ctx* c, uint64_t* n, uint64_t* n0, uint64_t* p) {
 
 ka_status ka_set_state(ka_ctx* c, const uint64_t* n, const uint64_t* n0, const uint64_t* p,
                        int64_t sweep, uint64_t seed) {
+  ka::NvtxRange nvtx_range("ka_set_state");
   if (!c || !n || !n0 || !p || sweep < 0 || sweep >= ((int64_t)1 << 32)) return KA_EINVAL;
   DeviceGuard dg(c->device);
   const size_t bytes = (size_t)c->pl.P * c->pl.plane_elems() * sizeof(uint64_t);

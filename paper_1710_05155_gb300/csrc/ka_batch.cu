@@ -482,6 +482,7 @@ ka_status ka_job_bytes(const ka_params* params, const ka_job_spec* spec, size_t*
 
 ka_status ka_batch_add(ka_batch* b, const ka_params* params, const ka_job_spec* spec,
                        int64_t* job_id) {
+  ka::NvtxRange nvtx_range("ka_batch_admit");
   if (!b || !params || !spec || spec->sweeps < 0 || spec->observe_every < 1) return KA_EINVAL;
   if (spec->sweeps >= ((int64_t)1 << 32)) return KA_EINVAL;
   ka_params prm = *params;
@@ -510,6 +511,7 @@ ka_status ka_batch_add(ka_batch* b, const ka_params* params, const ka_job_spec* 
 }
 
 ka_status ka_batch_adopt(ka_batch* b, ka_ctx* ctx, const ka_job_spec* spec, int64_t* job_id) {
+  ka::NvtxRange nvtx_range("ka_batch_admit");
   if (!b || !ctx || !spec || spec->observe_every < 1) return KA_EINVAL;
   if (spec->sweeps < ctx->sweep || spec->sweeps >= ((int64_t)1 << 32)) return KA_EINVAL;
   if (!ctx->owns || ctx->device != b->device) return KA_EINVAL;
@@ -522,6 +524,7 @@ ka_status ka_batch_adopt(ka_batch* b, ka_ctx* ctx, const ka_job_spec* spec, int6
 }
 
 ka_status ka_batch_step(ka_batch* b, int64_t max_sweeps, int64_t* sweeps_run) {
+  ka::NvtxRange nvtx_range("ka_batch_round");
   if (!b || max_sweeps < 0) return KA_EINVAL;
   int prev = -1;
   cudaGetDevice(&prev);
@@ -532,6 +535,7 @@ ka_status ka_batch_step(ka_batch* b, int64_t max_sweeps, int64_t* sweeps_run) {
 }
 
 ka_status ka_batch_autotune(ka_batch* b, int64_t* best_round) {
+  ka::NvtxRange nvtx_range("ka_batch_autotune");
   if (!b) return KA_EINVAL;
   int prev = -1;
   cudaGetDevice(&prev);

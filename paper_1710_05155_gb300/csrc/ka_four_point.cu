@@ -216,6 +216,7 @@ ka_status four_point_fail(ka_ctx* c, ka_status st, const std::string& msg) {
 }  // namespace
 
 extern "C" ka_status ka_four_point(ka_ctx* c, int32_t smax, int64_t* phi, int64_t* psi) {
+  ka::NvtxRange nvtx_range("ka_four_point");
   using namespace ka;
   if (!c) return KA_EINVAL;
   if (!phi || smax < 0) return four_point_fail(c, KA_EINVAL, "phi must be non-NULL, smax >= 0");

@@ -7,6 +7,8 @@
 // even W, else 1.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -18,6 +20,16 @@
 #define KA_HD __host__ __device__ __forceinline__
 
 namespace ka {
+
+// A named NVTX range for the lifetime of a scope (API calls show up by name
+// in profilers; costs nothing when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 
 constexpr uint32_t kTagInit = 0xFFFFFFFFu;   // counter word c1 of the initial-state keys
 constexpr uint32_t kTagGraph = 0xFFFFFFFEu;  // counter word c1 of the graph shuffle

@@ -207,6 +207,7 @@ cudaError_t launch_m(const SeqArgs& a, int m, unsigned words, size_t smem, cudaS
 }  // namespace ka
 
 extern "C" ka_status ka_sweep_sequential(ka_ctx* c, int64_t nsweeps) {
+  ka::NvtxRange nvtx_range("ka_sweep_sequential");
   using namespace ka;
   if (!c || nsweeps < 0) return KA_EINVAL;
   if (!c->initialized) {
