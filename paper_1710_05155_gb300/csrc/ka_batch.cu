@@ -56,7 +56,7 @@ struct GraphClass {
 };
 
 uint32_t cubic_tiles(int d, int L, int V, bool x) {
-  const int tp = 8 / V, win = 16 / V;
+  const int tp = ka::kCubicWarps / V, win = 2 * tp;
   int64_t np = 1;
   for (int k = 0; k < d - 1; ++k) np *= L;
   if (d >= 2) np /= 2;

@@ -53,12 +53,12 @@ namespace cubic {
 #ifndef KA_CUBIC_MIN_BLOCKS
 #define KA_CUBIC_MIN_BLOCKS 4
 #endif
-constexpr int kThreads = 256;  // 8 warps
-constexpr int kWarps = kThreads / 32;
+constexpr int kWarps = kCubicWarps;
+constexpr int kThreads = 32 * kWarps;
 // active pencils per CTA: 8 / V (mu = 0), or the active half of a
 // (16 / V)-column window along x (mu > 0)
 template <int V>
-__host__ __device__ constexpr int tp_of() { return 8 / V; }
+__host__ __device__ constexpr int tp_of() { return kWarps / V; }
 template <int V>
 __host__ __device__ constexpr int log2_of() { return V == 4 ? 2 : (V == 2 ? 1 : 0); }
 
@@ -252,9 +252,10 @@ __device__ __forceinline__ void build_info(const GroupArgs& a, const PencilMap<D
 // A thread keeps one pencil j and visits elements f = f0, f0 + step, ...
 //   mu = 0: a pencil is a row of L sites x V words; V warps share pencil
 //           warp % TP and their lanes walk consecutive elements of the row.
-//   mu > 0: the TP pencils of a window sit at x0 + 2j + off; the eight
-//           elements (j, h) of one row are lanes lane % 8, and a warp covers
-//           four rows (positions t = lane / 8 + 4 warp, step 32).
+//   mu > 0: the TP pencils of a window sit at x0 + 2j + off; the E = TP V
+//           elements (j, h) of one row are lanes lane % E, and a warp covers
+//           32 / E rows (positions t = lane / E + (32 / E) warp, step 32 / E
+//           times the warps).
 // Returns the position t and word h of element f.
 template <int V, bool X>
 __device__ __forceinline__ void elem_start(int warp, int lane, int& j, int& h, int& f0,
@@ -266,10 +267,11 @@ __device__ __forceinline__ void elem_start(int warp, int lane, int& j, int& h, i
     f0 = lane + 32 * (warp / TP);
     step = 32 * V;
   } else {
-    j = (lane & 7) / V;
-    h = (lane & 7) % V;
-    f0 = (lane >> 3) + 4 * warp;
-    step = 32;
+    constexpr int E = TP * V;  // elements (pencil, word) of one row: one lane each
+    j = (lane % E) / V;
+    h = (lane % E) % V;
+    f0 = lane / E + (32 / E) * warp;
+    step = (32 / E) * kWarps;
   }
 }
 
@@ -293,7 +295,7 @@ __device__ void unit_args(const CubicUnit& u, const BatchArgs& ba, GroupArgs& a)
   a.NP = 1;
   for (int k = 0; k < u.d - 1; ++k) a.NP *= u.L;
   if (u.d >= 2) a.NP /= 2;
-  const int win = 16 / V;
+  const int win = 2 * tp_of<V>();
   a.nwin = (u.L + win - 1) / win;
   a.PS = ((u.L + 15) / 16) * 16 + 1;
   const uint32_t t = u.t_base + ba.sweep_offset;

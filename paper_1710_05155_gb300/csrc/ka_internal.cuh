@@ -108,6 +108,10 @@ struct Planes {
   KA_HD size_t plane_elems() const { return (size_t)N * V; }
 };
 
+// Warps per CTA of the cubic pencil kernel: a tile holds kCubicWarps / V
+// active pencils (one warp per pencil-word in the compute phase).
+constexpr int kCubicWarps = 8;
+
 struct CubicShape {
   int d, L, m;
 };

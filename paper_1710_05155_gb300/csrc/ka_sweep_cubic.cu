@@ -43,7 +43,7 @@ cudaError_t launch_cubic_group(const Planes& pl, int q, const CubicShape& s, int
   a.NP = 1;
   for (int k = 0; k < d - 1; ++k) a.NP *= L;
   if (d >= 2) a.NP /= 2;
-  const int tp = 8 / V, win = 2 * tp;
+  const int tp = kCubicWarps / V, win = 2 * tp;
   a.nwin = (L + win - 1) / win;
   // the swizzle permutes slots inside aligned blocks of 16 entries; an odd
   // pencil stride keeps accesses across pencils on distinct banks
@@ -88,7 +88,7 @@ cudaError_t launch_cubic_group_batch(CubicUnit* units_dev, const uint32_t* tile_
   GroupArgs none{};
   none.ntiles = 0;
   const bool x = (mu == 0) || d == 1;
-  const int tp = 8 / V;
+  const int tp = kCubicWarps / V;
   const size_t smem = (size_t)2 * (2 + 2 * (d - 1)) * tp * V * PSmax * sizeof(uint64_t);
   return dispatch<true>(d, V, x, none, ba, m, ntiles, smem, st);
 }
