@@ -235,3 +235,38 @@ def test_large_rrg_prefix():
     sim.sweep(2)
     O.sweeps(topo, m, st, seed, 2)
     _assert_same(sim, st, "after 2 sweeps")
+
+
+def test_large_cubic_two_planes_sampled_words():
+    """d=3, L=128, 512 replicas (two planes of four words): the last word of each
+    plane against the oracle on those 64 replicas, after two sweeps."""
+    L, R, seed, rho = 128, 512, 3, 0.85
+    topo = O.cubic(3, L)
+    sim = K.Simulation(topo=K.KA_CUBIC, d=3, L=L, m=3, replicas=R)
+    assert sim.info["planes"] == 2 and sim.info["plane_words"] == 4
+    sim.init(seed, rho)
+    sim.sweep(2)
+    n, _, p = sim.get_state()
+    for w in (3, 7):
+        st = O.init(topo.N, 64, seed, rho, r0=64 * w)
+        O.sweeps(topo, 3, st, seed, 2)
+        assert (n[w] == O.pack_words(st.n)[0]).all()
+        assert (p[w] == O.pack_words(st.p)[0]).all()
+    sim.close()
+
+
+def test_large_rrg_four_word_planes_sampled_word():
+    """Random regular graph N=2^20, z=4, m=2, 256 replicas (one plane of four
+    words): the last word after two sweeps against the oracle on its 64 replicas."""
+    N, z, m, R, seed, rho = 1 << 20, 4, 2, 256, 2, 0.8
+    sim = K.Simulation(topo=K.KA_RRG, N=N, z=z, m=m, replicas=R, graph_seed=1)
+    assert sim.info["plane_words"] == 4
+    topo = O.rrg(N, z, 1)
+    sim.init(seed, rho)
+    sim.sweep(2)
+    n, _, p = sim.get_state()
+    st = O.init(N, 64, seed, rho, r0=192)
+    O.sweeps(topo, m, st, seed, 2)
+    assert (n[3] == O.pack_words(st.n)[0]).all()
+    assert (p[3] == O.pack_words(st.p)[0]).all()
+    sim.close()
