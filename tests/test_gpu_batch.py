@@ -138,3 +138,22 @@ def test_adopt_rules():
             sim.sweep(int(t) - sim.observe()[0])
             assert (sim.observe()[1] == c).all()
         sim.close()
+
+
+def test_out_of_memory_is_reported_and_harmless():
+    # about 2 TB of state: the allocation fails on the host side and nothing is left behind
+    big = dict(topo=K.KA_CUBIC, d=3, L=1024, m=3, replicas=4096)
+    params, keep = K.make_params(**big)
+    assert K.ka_required_bytes(params) > (1 << 40)
+    with pytest.raises(K.KaError) as e:
+        K.ka_create(params, keep)
+    assert e.value.status == K.KA_ENOMEM
+    with K.Batch(hbm_budget=1 << 62) as b:
+        with pytest.raises(K.KaError) as e:
+            b.add(10, 5, 1, 0.7, **big)
+        assert e.value.status == K.KA_ENOMEM
+        assert b.info()["jobs"] == 0 and b.info()["used_bytes"] == 0
+        jid = b.add(10, 5, 1, 0.7, topo=K.KA_CUBIC, d=3, L=16, m=3, replicas=64)
+        while b.info()["active"]:
+            b.step(5)
+        assert b.poll(jid) == (10, True)
