@@ -32,7 +32,7 @@ struct Job {
   int64_t* obs_dev = nullptr;  // [cap][R][4]
   std::vector<int64_t> obs_t;
   bool finished = false;
-  bool batched = true;  // false: cubic lattice on the edge-gather path, run with its own launches
+  bool batched = true;  // false: runs with its own (single-instance) launches inside each round
 };
 
 struct CubicClass {
@@ -86,6 +86,7 @@ struct ka_batch {
   int64_t exec_k = 0;
   int64_t last_k = 0;  // a round length is captured the second time it is used
   int64_t tuned_k = 16;
+  int64_t wave_tiles = 304;  // tiles one persistent launch of the pencil kernel runs at once
   std::string err;
 };
 
@@ -358,7 +359,7 @@ ka_status run_round(ka_batch* b, int64_t k_req, int64_t* ran) {
       e = issue_round(b, k);
     }
     if (e) return cuda_err(b, e, "round");
-    // jobs on the edge-gather path of a cubic lattice run with their own launches
+    // jobs not in the tables (large lattices, the edge-gather path) run with their own launches
     for (auto& kv : b->jobs) {
       Job* j = kv.second;
       if (j->finished || j->batched) continue;
@@ -425,7 +426,19 @@ ka_status enrol(ka_batch* b, ka_ctx* ctx, const ka_job_spec* spec, int64_t* job_
   j->target = spec->sweeps;
   j->every = spec->observe_every;
   j->cap = spec->sweeps / spec->observe_every + 2;
-  j->batched = !(ctx->topo == KA_CUBIC && !ctx->pencil);
+  // Small jobs share the batched launches.  A cubic lattice whose groups have
+  // a full wave of tiles on their own runs with its own launches (the
+  // single-instance kernel, arguments in the constant bank) -- as does a
+  // cubic lattice on the edge-gather path.
+  if (ctx->topo == KA_CUBIC) {
+    int64_t pencils = 1;
+    for (int k = 0; k < ctx->d - 1; ++k) pencils *= ctx->L;
+    if (ctx->d >= 2) pencils /= 2;
+    const int64_t tiles = (pencils + ka::kCubicWarps / ctx->pl.V - 1) / (ka::kCubicWarps / ctx->pl.V);
+    j->batched = ctx->pencil && tiles < b->wave_tiles;
+  } else {
+    j->batched = true;
+  }
   const ka_status st = observe_job(b, j);
   if (st) {
     cudaFree(j->obs_dev);
@@ -467,6 +480,11 @@ ka_status ka_batch_create(int32_t device, void* stream, size_t hbm_budget, int32
   }
   b->budget = hbm_budget;
   b->flags = flags;
+  {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
+      b->wave_tiles = 2 * (int64_t)sms;  // two CTAs of the pencil kernel per SM
+  }
   *out = b;
   return KA_OK;
 }
