@@ -161,61 +161,70 @@ class Server:
         def now() -> float:
             return self.clock() - t0
 
-        while pending or waiting or preparing or running:
-            t = now()
-            while pending and recs[pending[0]].arrival <= t:
-                waiting.append(pending.popleft())
-            # admission, in arrival order, against the memory budget
-            while waiting and len(preparing) < self.max_preparing:
-                r = recs[waiting[0]]
-                need = be.job_bytes(r.job)
-                if need > be.budget:
+        try:
+            while pending or waiting or preparing or running:
+                t = now()
+                while pending and recs[pending[0]].arrival <= t:
+                    waiting.append(pending.popleft())
+                # admission, in arrival order, against the memory budget
+                while waiting and len(preparing) < self.max_preparing:
+                    r = recs[waiting[0]]
+                    need = be.job_bytes(r.job)
+                    if need > be.budget:
+                        waiting.popleft()
+                        r.status, r.error, r.finished = "rejected", "larger than the budget", now()
+                        continue
+                    if be.used() + reserved + need > be.budget:
+                        break
                     waiting.popleft()
-                    r.status, r.error, r.finished = "rejected", "larger than the budget", now()
-                    continue
-                if be.used() + reserved + need > be.budget:
-                    break
-                waiting.popleft()
-                reserved += need
-                r.reserved, r.status = now(), "preparing"
-                preparing[be.prepare(r.job)] = (r, need)
-            # prepared contexts join the batch before its next round
-            for fut in [f for f in preparing if f.done()]:
-                r, need = preparing.pop(fut)
-                reserved -= need
+                    reserved += need
+                    r.reserved, r.status = now(), "preparing"
+                    preparing[be.prepare(r.job)] = (r, need)
+                # prepared contexts join the batch before its next round
+                for fut in [f for f in preparing if f.done()]:
+                    r, need = preparing.pop(fut)
+                    reserved -= need
+                    try:
+                        handle = fut.result()
+                    except Exception as e:  # a job that cannot be built fails alone
+                        r.status, r.error, r.finished = "failed", str(e), now()
+                        continue
+                    try:
+                        r.job_id = be.adopt(handle, r.job)
+                    except Exception as e:
+                        be.discard(handle)
+                        r.status, r.error, r.finished = "failed", str(e), now()
+                        continue
+                    r.admitted, r.status = now(), "running"
+                    running[r.job_id] = r
+                if running:
+                    max_running = max(max_running, len(running))
+                    s = self.clock()
+                    if not tuned and len(running) >= self.tune_at:
+                        be.autotune()
+                        tuned = True
+                    else:
+                        be.step(self.round_sweeps)
+                    busy += self.clock() - s
+                    rounds += 1
+                    for jid in [j for j in running if be.finished(j)]:
+                        r = running.pop(jid)
+                        r.finished, r.status = now(), "done"
+                        if self.keep_results:
+                            r.sweeps, r.counts = be.observations(jid, r.job.params["replicas"])
+                        be.remove(jid)
+                elif preparing:
+                    cf.wait(list(preparing), timeout=0.01, return_when=cf.FIRST_COMPLETED)
+                elif pending and not waiting:
+                    self.sleep(min(0.01, max(0.0, recs[pending[0]].arrival - now())))
+        finally:
+            # on an early exit, contexts still being prepared are never adopted:
+            # release them (the batch frees its own jobs when it is closed)
+            for fut in preparing:
                 try:
-                    handle = fut.result()
-                except Exception as e:  # a job that cannot be built fails alone
-                    r.status, r.error, r.finished = "failed", str(e), now()
-                    continue
-                try:
-                    r.job_id = be.adopt(handle, r.job)
-                except Exception as e:
-                    be.discard(handle)
-                    r.status, r.error, r.finished = "failed", str(e), now()
-                    continue
-                r.admitted, r.status = now(), "running"
-                running[r.job_id] = r
-            if running:
-                max_running = max(max_running, len(running))
-                s = self.clock()
-                if not tuned and len(running) >= self.tune_at:
-                    be.autotune()
-                    tuned = True
-                else:
-                    be.step(self.round_sweeps)
-                busy += self.clock() - s
-                rounds += 1
-                for jid in [j for j in running if be.finished(j)]:
-                    r = running.pop(jid)
-                    r.finished, r.status = now(), "done"
-                    if self.keep_results:
-                        r.sweeps, r.counts = be.observations(jid, r.job.params["replicas"])
-                    be.remove(jid)
-            elif preparing:
-                cf.wait(list(preparing), timeout=0.01, return_when=cf.FIRST_COMPLETED)
-            elif pending and not waiting:
-                self.sleep(min(0.01, max(0.0, recs[pending[0]].arrival - now())))
+                    be.discard(fut.result())
+                except Exception:
+                    pass
         return self.report(busy, rounds, max_running)
 
     def report(self, busy: float, rounds: int, max_running: int) -> dict:

@@ -189,3 +189,33 @@ def test_scaled_sample():
         assert y.sweeps == max(1, round(x.sweeps * 0.1))
         assert y.arrival == pytest.approx(x.arrival / 2)
         assert y.params == x.params and y.seed == x.seed
+
+
+def test_contexts_in_preparation_are_released_on_failure():
+    import threading
+
+    class Failing(FakeBackend):
+        def __init__(self, clock):
+            super().__init__(clock, budget=1000)
+            self.discarded = []
+
+        def prepare(self, job):
+            f = cf.Future()
+            if job.tag["index"] == 0:
+                f.set_result(job)  # ready at once: adopted, then the round fails
+            else:
+                threading.Timer(0.05, f.set_result, args=(job,)).start()
+            return f
+
+        def discard(self, handle):
+            self.discarded.append(handle.tag["index"])
+
+        def step(self, k):
+            raise RuntimeError("device lost")
+
+    clock = FakeClock()
+    be = Failing(clock)
+    srv = serve.Server(be, clock=clock, sleep=clock.sleep, autotune=False)
+    with pytest.raises(RuntimeError):
+        srv.run([job(i, 0.0, 10, 10) for i in range(3)])
+    assert sorted(be.discarded) == [1, 2]
