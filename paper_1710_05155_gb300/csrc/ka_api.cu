@@ -157,6 +157,8 @@ ka_status create_common(const ka_params* params, void* buf, size_t bytes, bool o
   c->is.pre_idx = (uint32_t*)(base + l.pre_idx);
   c->is.krem = (int64_t*)(base + l.krem);
   c->is.unresolved = (int32_t*)(base + l.unresolved);
+  c->is.cand = c->stage ? (uint32_t*)c->stage : nullptr;  // idle during init
+  c->is.cand_bytes = c->stage ? (size_t)s.N * s.W * sizeof(uint64_t) : 0;
 
   std::string msg;
   if (s.topo == KA_CUBIC) {

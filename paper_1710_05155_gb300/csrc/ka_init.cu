@@ -9,9 +9,17 @@
 // The K-th smallest composite key of every replica is found exactly by a
 // most-significant-digit radix select over 8-bit digits: eight passes over
 // the 64-bit key, then (only if some replica's threshold key is tied)
-// passes over the site index.  Keys are recomputed in every pass instead of
-// stored, which keeps the scratch at R x 256 counters.  A final pass writes
-// the bit planes: n = [composite <= threshold], n0 = n, p = all ones.
+// passes over the site index.  Keys are recomputed instead of stored, which
+// keeps the scratch at R x 256 counters.  When the context has room (its
+// staging plane, idle during init), the sites whose key shares the threshold's
+// top byte -- about N / 256 per replica -- are collected into per-replica
+// lists after the first pass, and the later passes evaluate only those; a list
+// that would overflow its capacity sends the later passes back to scanning
+// all sites.  A final pass writes the bit planes: n = [composite <=
+// threshold], n0 = n, p = all ones.
+#include <algorithm>
+#include <vector>
+
 #include "ka_internal.cuh"
 
 namespace ka {
@@ -21,6 +29,9 @@ constexpr int kSitesPerThread = 32;
 
 struct InitArgs {
   uint32_t* hist;
+  uint32_t* cand_n;  // [R] candidates collected per replica
+  uint32_t* cand;    // [R][cap] their site indices
+  int64_t cap;
   uint64_t* pre_key;
   uint32_t* pre_idx;
   int64_t* krem;
@@ -75,6 +86,58 @@ __global__ void __launch_bounds__(256) k_init_hist(const InitArgs a) {
   for (int k = threadIdx.x; k < 512; k += blockDim.x) {
     const uint32_t c = (&sh[0][0])[k];
     if (c) atomicAdd(&a.hist[(size_t)(r0 + (k >> 8)) * 256 + (k & 255)], c);
+  }
+}
+
+// After pass 0: collect the sites whose key has the threshold's top byte
+// (the only ones later passes can count), per replica.
+__global__ void __launch_bounds__(256) k_init_collect(const InitArgs a) {
+  const int rp = blockIdx.y;
+  const int r0 = 2 * rp;
+  const bool live0 = a.krem[r0] > 0, live1 = a.krem[r0 + 1] > 0;
+  if (!live0 && !live1) return;
+  const uint64_t top0 = a.pre_key[r0] >> 56, top1 = a.pre_key[r0 + 1] >> 56;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kSitesPerThread + threadIdx.x;
+  for (int s = 0; s < kSitesPerThread; ++s) {
+    const int64_t i = i0 + (int64_t)s * blockDim.x;
+    if (i >= a.N) break;
+    const uint4 b = philox(make_uint4((uint32_t)rp, kTagInit, (uint32_t)i, 0u), a.rk);
+    if (live0 && (lo64(b) >> 56) == top0) {
+      const uint32_t k = atomicAdd(&a.cand_n[r0], 1u);
+      if (k < (uint64_t)a.cap) a.cand[(size_t)r0 * a.cap + k] = (uint32_t)i;
+    }
+    if (live1 && (hi64(b) >> 56) == top1) {
+      const uint32_t k = atomicAdd(&a.cand_n[r0 + 1], 1u);
+      if (k < (uint64_t)a.cap) a.cand[(size_t)(r0 + 1) * a.cap + k] = (uint32_t)i;
+    }
+  }
+}
+
+// a histogram pass over the candidate list of each replica (grid: x over
+// list chunks, y over replicas)
+__global__ void __launch_bounds__(256) k_init_hist_cand(const InitArgs a) {
+  __shared__ uint32_t sh[256];
+  const int r = blockIdx.y;
+  if (a.pass >= 8 && *a.unresolved == 0) return;  // uniform early exit
+  if (a.krem[r] <= 0) return;
+  for (int k = threadIdx.x; k < 256; k += blockDim.x) sh[k] = 0;
+  __syncthreads();
+  const int64_t n = a.cand_n[r];
+  const uint64_t pk = a.pre_key[r];
+  const uint32_t pi = a.pre_idx[r];
+  const int64_t c0 = (int64_t)blockIdx.x * blockDim.x * kSitesPerThread + threadIdx.x;
+  for (int s = 0; s < kSitesPerThread; ++s) {
+    const int64_t c = c0 + (int64_t)s * blockDim.x;
+    if (c >= n) break;
+    const uint32_t i = a.cand[(size_t)r * a.cap + c];
+    const uint4 b = philox(make_uint4((uint32_t)(r >> 1), kTagInit, i, 0u), a.rk);
+    int dg;
+    if (digit_of(a, (r & 1) ? hi64(b) : lo64(b), i, pk, pi, dg)) atomicAdd(&sh[dg], 1u);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < 256; k += blockDim.x) {
+    const uint32_t v = sh[k];
+    if (v) atomicAdd(&a.hist[(size_t)r * 256 + k], v);
   }
 }
 
@@ -210,9 +273,46 @@ cudaError_t launch_init(const Planes& pl, const InitScratch& s, int R, int64_t K
   const int64_t chunk = 256LL * kSitesPerThread;
   dim3 hgrid((unsigned)((pl.N + chunk - 1) / chunk), (unsigned)(R / 2));
   const int passes = 8 + a.idx_bits / 8;
+  // candidate lists: about N / 256 entries expected per replica; take them
+  // when the room holds N / 128 + 1024 (a list longer than that falls back)
+  a.cand_n = nullptr;
+  a.cand = nullptr;
+  a.cap = 0;
+  bool lists = false;
+  if (s.cand && pl.N >= 65536) {
+    const int64_t room = (int64_t)(s.cand_bytes / sizeof(uint32_t)) - R;
+    const int64_t cap = room / R;
+    if (cap >= pl.N / 128 + 1024) {
+      a.cand_n = s.cand;
+      a.cand = s.cand + R;
+      a.cap = cap;
+      lists = true;
+    }
+  }
   for (int p = 0; p < passes; ++p) {
     a.pass = p;
-    k_init_hist<<<hgrid, 256, 0, st>>>(a);
+    if (lists && p == 1) {
+      // collect the candidates of every replica, then check the lists fit
+      if ((err = cudaMemsetAsync(a.cand_n, 0, (size_t)R * sizeof(uint32_t), st))) return err;
+      k_init_collect<<<hgrid, 256, 0, st>>>(a);
+      if ((err = cudaGetLastError())) return err;
+      std::vector<uint32_t> counts(R);
+      if ((err = cudaMemcpyAsync(counts.data(), a.cand_n, (size_t)R * sizeof(uint32_t),
+                                 cudaMemcpyDeviceToHost, st)))
+        return err;
+      if ((err = cudaStreamSynchronize(st))) return err;
+      int64_t longest = 0;
+      for (uint32_t c : counts) longest = std::max<int64_t>(longest, c);
+      lists = longest <= a.cap;
+    }
+    if (lists && p >= 1) {
+      const int64_t cchunk = 256LL * kSitesPerThread;
+      const unsigned cx = (unsigned)std::max<int64_t>(1, (a.cap + cchunk - 1) / cchunk);
+      // the grid covers the capacity; blocks past a replica's count return at once
+      k_init_hist_cand<<<dim3(cx, (unsigned)R), 256, 0, st>>>(a);
+    } else {
+      k_init_hist<<<hgrid, 256, 0, st>>>(a);
+    }
     if ((err = cudaGetLastError())) return err;
     k_init_select<<<(R + 7) / 8, 256, 0, st>>>(a, R);
     if ((err = cudaGetLastError())) return err;

@@ -189,6 +189,10 @@ struct InitScratch {
   uint32_t* pre_idx;   // [R] decided high bits of the threshold site
   int64_t* krem;       // [R] rank still to place inside the current bucket
   int32_t* unresolved; // [1] any replica whose threshold key is tied
+  // optional: room for per-replica candidate lists (the staging plane, idle
+  // during init); null or too small -> every pass scans all sites
+  uint32_t* cand;
+  size_t cand_bytes;
 };
 cudaError_t launch_init(const Planes& pl, const InitScratch& s, int R, int64_t K,
                         const RoundKeys& rk, cudaStream_t st);

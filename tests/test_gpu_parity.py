@@ -270,3 +270,22 @@ def test_large_rrg_four_word_planes_sampled_word():
     assert (n[3] == O.pack_words(st.n)[0]).all()
     assert (p[3] == O.pack_words(st.p)[0]).all()
     sim.close()
+
+
+@pytest.mark.parametrize("kw,rho", [
+    (dict(topo=K.KA_CUBIC, d=3, L=48, m=3, replicas=128), 0.3),   # two-word planes: candidate lists
+    (dict(topo=K.KA_CUBIC, d=3, L=48, m=3, replicas=128), 0.85),
+    (dict(topo=K.KA_CUBIC, d=3, L=64, m=3, replicas=256), 0.5),   # four-word planes
+    (dict(topo=K.KA_CUBIC, d=3, L=48, m=3, replicas=64), 0.6),    # one-word planes: full scans
+])
+def test_initial_state_of_larger_lattices(kw, rho):
+    """The initial state (exactly K particles per replica, the K smallest
+    Philox keys) of lattices large enough for the candidate-list passes."""
+    sim = K.Simulation(**kw)
+    sim.init(19, rho)
+    n, n0, p = sim.get_state()
+    N = kw["L"] ** kw["d"]
+    st = O.init(N, kw["replicas"], 19, rho)
+    assert (n == O.pack_words(st.n)).all() and (n0 == n).all()
+    assert (p == np.uint64(0xFFFFFFFFFFFFFFFF)).all()
+    sim.close()
