@@ -289,3 +289,15 @@ def test_initial_state_of_larger_lattices(kw, rho):
     assert (n == O.pack_words(st.n)).all() and (n0 == n).all()
     assert (p == np.uint64(0xFFFFFFFFFFFFFFFF)).all()
     sim.close()
+
+
+@pytest.mark.parametrize("kw", [
+    dict(topo=K.KA_CUBIC, d=2, L=132, m=2, replicas=64),    # above the pencil kernel's L <= 128
+    dict(topo=K.KA_CUBIC, d=1, L=256, m=1, replicas=128),   # edge-gather path, two-word planes
+    dict(topo=K.KA_CUBIC, d=4, L=16, m=5, replicas=256),    # d = 4 with four-word planes
+    dict(topo=K.KA_CUBIC, d=2, L=128, m=3, replicas=256),   # the pencil kernel's longest pencils
+    dict(topo=K.KA_RRG, N=4096, z=4, m=0, replicas=256, graph_seed=6),   # m = 0, four-word planes
+    dict(topo=K.KA_RRG, N=4096, z=4, m=3, replicas=256, graph_seed=7),   # m = z - 1: no constraint
+], ids=lambda k: "-".join(f"{a}{b}" for a, b in k.items() if a != "topo"))
+def test_edge_shapes_every_sweep(kw):
+    _run_case(dict(kw), seed=23, rho=0.64, sweeps=3)
