@@ -29,6 +29,11 @@ JOBS = [
     dict(params=dict(topo=K.KA_RRG, N=1000, z=3, m=1, replicas=64, graph_seed=3), sweeps=14, every=14, seed=12, rho=0.7),
     dict(params=dict(topo=K.KA_RRG, N=3000, z=4, m=2, replicas=256, graph_seed=4), sweeps=13, every=5, seed=14, rho=0.8),
     dict(params=dict(topo=K.KA_CUBIC, d=3, L=8, m=3, replicas=64, flags=K.KA_FLAG_GENERIC), sweeps=11, every=3, seed=13, rho=0.7),
+    # a caller-supplied graph: the layered random graph of section 5.2
+    dict(params=dict(topo=K.KA_GRAPH, N=4 * 4 ** 3, z=6, m=3, replicas=128,
+                     nbr=K.ka_layered_graph(3, 4, 4, 9)), sweeps=16, every=4, seed=15, rho=0.72),
+    # a cubic lattice large enough to run with its own launches inside the rounds
+    dict(params=dict(topo=K.KA_CUBIC, d=3, L=64, m=3, replicas=64), sweeps=6, every=3, seed=16, rho=0.8),
 ]
 
 
