@@ -10,10 +10,18 @@
 // are the up and down neighbours along mu on a cubic lattice; on a graph the
 // slots follow the neighbour row, kept in ascending order).
 //
-// The attempts of one word form a chain, so one warp runs one word: its 32
-// lanes draw 32 attempts at a time (the draws do not depend on the state),
-// then lane 0 applies them in order.  The word's n and p planes sit in shared
-// memory when they fit, else the chain works on global memory.
+// The attempts of one word form a chain; one warp runs one word and applies
+// its attempts 32 at a time, one per lane, with the result of the chain in
+// order.  An attempt reads n on its read set R = {i, j} and the neighbours
+// of i and of j, and writes n and p on W = {i, j}.  Attempts k and l
+// conflict when W_k meets R_l or W_l meets R_k.  The warp applies the
+// pending attempts in rounds: in each, every pending attempt that conflicts
+// with no earlier pending attempt (a set that always holds the earliest)
+// reads, decides and writes.  Such an attempt sees exactly the state the
+// chain would give it: no earlier attempt still pending writes what it
+// reads, and it writes nothing that an earlier pending attempt has yet to
+// read; attempts applied in one round touch disjoint sites.  The word's n
+// and p planes sit in shared memory when they fit, else in global memory.
 #include <algorithm>
 #include <string>
 
@@ -126,24 +134,44 @@ __global__ void __launch_bounds__(32) k_sequential(const __grid_constant__ SeqAr
     st = 1;
   }
   const uint64_t range = (uint64_t)a.N * (uint64_t)a.z;
+  const uint32_t earlier = (1u << lane) - 1u;  // lanes of the earlier attempts
   for (int s = 0; s < a.nsweeps; ++s) {
     const uint32_t t = a.t0 + (uint32_t)s;
     for (int64_t k0 = 0; k0 < a.N; k0 += 32) {
       const int64_t k = k0 + lane;
-      const uint64_t r = (k < a.N) ? draw_bond(a.rk, t, (uint32_t)k, w, range) : 0ull;
-      const int cnt = (a.N - k0) < 32 ? (int)(a.N - k0) : 32;
-      for (int l = 0; l < cnt; ++l) {
-        const uint64_t rl = __shfl_sync(0xffffffffu, r, l);
-        if (lane == 0) {
-          const uint32_t i = (uint32_t)(rl / (uint64_t)a.z);
-          uint32_t ni_[8], nj_[8];
-          neighbours(a, i, ni_);
-          const int sel = (int)(rl % (uint64_t)a.z);
-          uint32_t j = 0;
+      const bool live = k < a.N;
+      const uint64_t r = live ? draw_bond(a.rk, t, (uint32_t)k, w, range) : 0ull;
+      // this lane's bond (i, j) and the neighbours of both
+      const uint32_t i = (uint32_t)(r / (uint64_t)a.z);
+      const int sel = (int)(r % (uint64_t)a.z);
+      uint32_t ni_[8], nj_[8];
+      neighbours(a, i, ni_);
+      uint32_t j = 0;
 #pragma unroll
-          for (int s2 = 0; s2 < 8; ++s2)
-            if (s2 == sel) j = ni_[s2];
-          neighbours(a, j, nj_);
+      for (int s2 = 0; s2 < 8; ++s2)
+        if (s2 == sel) j = ni_[s2];
+      neighbours(a, j, nj_);
+      // bit o of conf: attempt o writes a site this attempt reads
+      uint32_t conf = 0;
+      for (int o = 0; o < 32; ++o) {
+        const uint32_t io = __shfl_sync(0xffffffffu, i, o), jo = __shfl_sync(0xffffffffu, j, o);
+        uint32_t hit = (io == i) | (io == j) | (jo == i) | (jo == j);
+#pragma unroll
+        for (int slot = 0; slot < 8; ++slot) {
+          if (slot >= a.z) break;
+          hit |= (ni_[slot] == io) | (ni_[slot] == jo) | (nj_[slot] == io) | (nj_[slot] == jo);
+        }
+        conf |= hit << o;
+      }
+      // and the other way round (transpose of the warp's bit matrix)
+      for (int o = 0; o < 32; ++o) {
+        const uint32_t col = __ballot_sync(0xffffffffu, (conf >> o) & 1u);
+        if (lane == o) conf |= col;
+      }
+      uint32_t pending = __ballot_sync(0xffffffffu, live);
+      while (pending) {
+        const bool ready = ((pending >> lane) & 1u) && !(conf & pending & earlier);
+        if (ready) {
           const uint64_t vi = n[(int64_t)i * st], vj = n[(int64_t)j * st];
           uint64_t ci2 = 0, ci1 = 0, ci0 = 0, cj2 = 0, cj1 = 0, cj0 = 0;
 #pragma unroll
@@ -162,6 +190,7 @@ __global__ void __launch_bounds__(32) k_sequential(const __grid_constant__ SeqAr
             p[(int64_t)j * st] &= ~sw;
           }
         }
+        pending &= ~__ballot_sync(0xffffffffu, ready);
         __syncwarp();
       }
     }
