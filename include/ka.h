@@ -152,9 +152,11 @@ ka_status ka_sweep(ka_ctx *ctx, int64_t n);
  * i = r / z and its neighbour in slot r mod z (on cubic lattices slot 2 mu is
  * the up and 2 mu + 1 the down neighbour along mu; on graphs the slots are
  * the neighbour row in ascending order, as ka_graph_tables returns it).  One warp per word runs
- * the chain, in shared memory when the lattice has at most 10240 sites; it is
- * a reference schedule, not a fast one.  Advances the sweep counter; no
- * synchronisation.  KA_ESTATE before init, KA_EINVAL if N z >= 2^32. */
+ * the chain, 32 attempts at a time, applying together the attempts that do
+ * not touch each other's sites (the result is the in-order chain's), in
+ * shared memory when the lattice has at most 10240 sites.  Advances the sweep
+ * counter; no synchronisation.  KA_ESTATE before init, KA_EINVAL if
+ * N z >= 2^32. */
 ka_status ka_sweep_sequential(ka_ctx *ctx, int64_t n);
 
 /* Observables of the current state into host int64 counts[R][4]; writes the

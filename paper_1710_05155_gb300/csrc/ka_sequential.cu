@@ -14,7 +14,11 @@
 // its attempts 32 at a time, one per lane, with the result of the chain in
 // order.  An attempt reads n on its read set R = {i, j} and the neighbours
 // of i and of j, and writes n and p on W = {i, j}.  Attempts k and l
-// conflict when W_k meets R_l or W_l meets R_k.  The warp applies the
+// conflict when W_k meets R_l or W_l meets R_k: every attempt sets its lane
+// bit in a shared-memory stamp word of both sites of W, then ORs the stamps
+// over R (sites share a stamp modulo the table size when N is larger; a shared
+// stamp can only add conflicts), and a transpose by ballots adds the other
+// direction.  The warp applies the
 // pending attempts in rounds: in each, every pending attempt that conflicts
 // with no earlier pending attempt (a set that always holds the earliest)
 // reads, decides and writes.  Such an attempt sees exactly the state the
@@ -32,6 +36,7 @@ namespace {
 
 constexpr uint32_t kTagSequential = 0xFFFFFFFCu;
 constexpr int kSmemWords = 20480;  // n and p of up to 10240 sites in shared memory
+constexpr uint32_t kStampsGlobal = 32768;  // stamp words when the planes stay in global memory
 
 struct SeqArgs {
   uint64_t* n;
@@ -42,6 +47,7 @@ struct SeqArgs {
   size_t plane_elems;
   uint32_t t0;
   int nsweeps;
+  uint32_t hmask;  // stamp words - 1 (a power of two)
   RoundKeys rk;
 };
 
@@ -133,6 +139,10 @@ __global__ void __launch_bounds__(32) k_sequential(const __grid_constant__ SeqAr
     p = sm + a.N;
     st = 1;
   }
+  uint32_t* stamp = reinterpret_cast<uint32_t*>(sm + (SMEM ? 2 * a.N : 0));
+  const uint32_t hm = a.hmask;
+  for (uint32_t b = lane; b <= hm; b += 32) stamp[b] = 0;
+  __syncwarp();
   const uint64_t range = (uint64_t)a.N * (uint64_t)a.z;
   const uint32_t earlier = (1u << lane) - 1u;  // lanes of the earlier attempts
   for (int s = 0; s < a.nsweeps; ++s) {
@@ -151,18 +161,25 @@ __global__ void __launch_bounds__(32) k_sequential(const __grid_constant__ SeqAr
       for (int s2 = 0; s2 < 8; ++s2)
         if (s2 == sel) j = ni_[s2];
       neighbours(a, j, nj_);
-      // bit o of conf: attempt o writes a site this attempt reads
-      uint32_t conf = 0;
-      for (int o = 0; o < 32; ++o) {
-        const uint32_t io = __shfl_sync(0xffffffffu, i, o), jo = __shfl_sync(0xffffffffu, j, o);
-        uint32_t hit = (io == i) | (io == j) | (jo == i) | (jo == j);
-#pragma unroll
-        for (int slot = 0; slot < 8; ++slot) {
-          if (slot >= a.z) break;
-          hit |= (ni_[slot] == io) | (ni_[slot] == jo) | (nj_[slot] == io) | (nj_[slot] == jo);
-        }
-        conf |= hit << o;
+      // bit o of conf: attempt o writes a site this attempt reads (or one
+      // sharing its stamp)
+      if (live) {
+        atomicOr(&stamp[i & hm], 1u << lane);
+        atomicOr(&stamp[j & hm], 1u << lane);
       }
+      __syncwarp();
+      uint32_t conf = stamp[i & hm] | stamp[j & hm];
+#pragma unroll
+      for (int slot = 0; slot < 8; ++slot) {
+        if (slot >= a.z) break;
+        conf |= stamp[ni_[slot] & hm] | stamp[nj_[slot] & hm];
+      }
+      __syncwarp();
+      if (live) {
+        stamp[i & hm] = 0;
+        stamp[j & hm] = 0;
+      }
+      __syncwarp();
       // and the other way round (transpose of the warp's bit matrix)
       for (int o = 0; o < 32; ++o) {
         const uint32_t col = __ballot_sync(0xffffffffu, (conf >> o) & 1u);
@@ -268,14 +285,29 @@ extern "C" ka_status ka_sweep_sequential(ka_ctx* c, int64_t nsweeps) {
   a.rk = c->rk;
   const unsigned words = (unsigned)(c->R / 64);
   const bool smem = 2 * c->N <= kSmemWords;
+  // stamp table: one word per site when the planes are in shared memory
+  // (exact), else kStampsGlobal words shared modulo their count
+  uint32_t H = 32;
+  if (smem) {
+    while ((int64_t)H < c->N) H <<= 1;
+  } else {
+    H = kStampsGlobal;
+  }
+  a.hmask = H - 1;
+  const size_t smem_bytes = (smem ? (size_t)2 * c->N * sizeof(uint64_t) : 0) + (size_t)H * 4;
+  if (smem_bytes > (size_t)227 * 1024) {
+    if (prev >= 0) cudaSetDevice(prev);
+    c->err = "sequential sweep: shared memory plan too large";
+    return KA_EINVAL;
+  }
   // launches of at most about 2^20 attempts each
   const int64_t chunk = std::max<int64_t>(1, ((int64_t)1 << 20) / c->N);
   cudaError_t e = cudaSuccess;
   for (int64_t done = 0; done < nsweeps && !e; done += chunk) {
     a.t0 = (uint32_t)(c->sweep + done);
     a.nsweeps = (int)std::min<int64_t>(chunk, nsweeps - done);
-    e = smem ? launch_m<true>(a, c->m, words, (size_t)2 * c->N * sizeof(uint64_t), c->stream)
-             : launch_m<false>(a, c->m, words, 0, c->stream);
+    e = smem ? launch_m<true>(a, c->m, words, smem_bytes, c->stream)
+             : launch_m<false>(a, c->m, words, smem_bytes, c->stream);
   }
   if (prev >= 0) cudaSetDevice(prev);
   if (e) {

@@ -2,7 +2,7 @@
 
 Every word of n, n0, p and every count must equal the oracle's after every sweep: cubic
 lattices from coordinates (one-, two- and four-word planes; shared-memory and global-memory
-chains), the edge-gather tables, random regular and layered graphs, and sequential sweeps
+chains, with exact and shared conflict stamps), the edge-gather tables, random regular and layered graphs, and sequential sweeps
 after class sweeps (the sweep counter keys both streams).
 """
 import numpy as np
@@ -43,6 +43,8 @@ CASES = [
     dict(topo=K.KA_CUBIC, d=3, L=8, m=3, replicas=256),
     dict(topo=K.KA_CUBIC, d=1, L=32, m=0, replicas=192),
     dict(topo=K.KA_CUBIC, d=3, L=24, m=3, replicas=64),   # 13824 sites: global-memory chain
+    dict(topo=K.KA_CUBIC, d=2, L=256, m=2, replicas=64),  # 65536 sites: sites share stamp words
+    dict(topo=K.KA_CUBIC, d=4, L=8, m=5, replicas=64),    # z = 8
     dict(topo=K.KA_CUBIC, d=3, L=8, m=2, replicas=64, flags=K.KA_FLAG_GENERIC),
     dict(topo=K.KA_RRG, N=1000, z=3, m=1, replicas=128, graph_seed=4),
     dict(topo=K.KA_RRG, N=2048, z=4, m=2, replicas=256, graph_seed=5),
