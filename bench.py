@@ -265,7 +265,10 @@ def run_native(args, rank: int, world: int) -> None:
     traffic = measured_traffic()
 
     # end to end through the C ABI: initial state from pinned host memory,
-    # S sweeps, counts back to the host, for every context
+    # S sweeps, counts back to the host, for every context.  Each context runs
+    # on its own stream: its state is uploaded (ka_set_state_async) while the
+    # previous context sweeps, and its sweeps wait for the previous context's
+    # to finish, so that one context at a time holds the L2.
     host_init = []
     for sim in sims:
         n, n0, p = sim.get_state()
@@ -278,10 +281,20 @@ def run_native(args, rank: int, world: int) -> None:
     out = [np.zeros((R, 4), np.int64) for _ in sims]
     e2e_steps = max(2, min(args.steps, 5))
 
+    e2e_streams = [torch.cuda.Stream(dev) for _ in sims]
+    e2e_sims = [K.Simulation(topo=K.KA_CUBIC, d=D, L=L, m=M, replicas=R, device=dev, stream=st)
+                for st in e2e_streams]
+
     def e2e_step():
-        for sim, hs, o in zip(sims, host_init, out):
-            K.ka_set_state(sim.ctx, hs[0], hs[1], hs[2], 0, SEED)
+        prev = None
+        for sim, st, hs in zip(e2e_sims, e2e_streams, host_init):
+            K.ka_set_state_async(sim.ctx, hs[0], hs[1], hs[2], 0, SEED)
+            if prev is not None:
+                st.wait_event(prev)
             K.ka_sweep(sim.ctx, S)
+            prev = torch.cuda.Event()
+            prev.record(st)
+        for sim, o in zip(e2e_sims, out):
             K.ka_observe(sim.ctx, o)
 
     e2e_step()
@@ -333,7 +346,7 @@ def run_native(args, rank: int, world: int) -> None:
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
-    for sim in sims:
+    for sim in sims + e2e_sims:
         sim.close()
     if dist:
         dist.destroy_process_group()

@@ -194,6 +194,17 @@ ka_status ka_get_state(ka_ctx *ctx, uint64_t *n, uint64_t *n0, uint64_t *p);
 ka_status ka_set_state(ka_ctx *ctx, const uint64_t *n, const uint64_t *n0, const uint64_t *p,
                        int64_t sweep, uint64_t seed);
 
+/* ka_set_state without the synchronisation: the copies (and, for V > 1, the
+ * layout conversion) are queued on the context's stream and the call
+ * returns.  The host arrays must stay valid and unchanged until that work
+ * has run (ka_sync, or any later synchronising call on the context).  From
+ * page-locked host memory the copies run asynchronously to the host and can
+ * overlap other streams' kernels; from pageable memory the call may return
+ * only once they are done.  Errors as ka_set_state; copy errors may also
+ * surface at the next synchronising call. */
+ka_status ka_set_state_async(ka_ctx *ctx, const uint64_t *n, const uint64_t *n0,
+                             const uint64_t *p, int64_t sweep, uint64_t seed);
+
 /* Wait for all work of the context; reports deferred kernel errors. */
 ka_status ka_sync(ka_ctx *ctx);
 

@@ -67,6 +67,8 @@ _SIGS = {
     "ka_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ka_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                C.c_uint64]),
+    "ka_set_state_async": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                     C.c_uint64]),
     "ka_sync": (C.c_int, [C.c_void_p]),
     "ka_info": (C.c_int, [C.c_void_p, _P(ka_info_t)]),
     "ka_graph_tables": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -131,6 +133,7 @@ class Ctx:
         self.handle = C.c_void_p(handle)
         self._keep = keep  # any objects the context must not outlive
         self.info = None
+        self.inflight = []  # host arrays of queued copies, until the next synchronisation
 
     def __bool__(self):
         return bool(self.handle.value)
@@ -220,6 +223,7 @@ def ka_observe(ctx: Ctx, out: np.ndarray | None = None):
         out = np.zeros((R, 4), np.int64)
     sweep = C.c_int64(0)
     _check(load().ka_observe(ctx.handle, C.byref(sweep), _ptr(out)), "ka_observe", ctx)
+    ctx.inflight.clear()
     return sweep.value, out
 
 
@@ -245,6 +249,7 @@ def ka_get_state(ctx: Ctx):
     shape = (info["words"], info["N"])
     n, n0, p = (np.zeros(shape, np.uint64) for _ in range(3))
     _check(load().ka_get_state(ctx.handle, _ptr(n), _ptr(n0), _ptr(p)), "ka_get_state", ctx)
+    ctx.inflight.clear()
     return n, n0, p
 
 
@@ -252,10 +257,25 @@ def ka_set_state(ctx: Ctx, n, n0, p, sweep: int, seed: int) -> None:
     n, n0, p = (np.ascontiguousarray(x, np.uint64) for x in (n, n0, p))
     _check(load().ka_set_state(ctx.handle, _ptr(n), _ptr(n0), _ptr(p), sweep, seed),
            "ka_set_state", ctx)
+    ctx.inflight.clear()
+
+
+def ka_set_state_async(ctx: Ctx, n, n0, p, sweep: int, seed: int) -> None:
+    """ka_set_state queued on the context's stream without synchronising.  n, n0
+    and p must be C-contiguous uint64 arrays (page-locked for the copies to be
+    asynchronous); they are kept referenced until the next ka_sync of ctx and
+    must not be changed before it."""
+    for x in (n, n0, p):
+        if not (isinstance(x, np.ndarray) and x.dtype == np.uint64 and x.flags.c_contiguous):
+            raise ValueError("ka_set_state_async needs C-contiguous uint64 arrays")
+    _check(load().ka_set_state_async(ctx.handle, _ptr(n), _ptr(n0), _ptr(p), sweep, seed),
+           "ka_set_state_async", ctx)
+    ctx.inflight.append((n, n0, p))
 
 
 def ka_sync(ctx: Ctx) -> None:
     _check(load().ka_sync(ctx.handle), "ka_sync", ctx)
+    ctx.inflight.clear()
 
 
 def ka_graph_tables(ctx: Ctx) -> dict:
@@ -438,6 +458,9 @@ class Simulation:
 
     def set_state(self, n, n0, p, sweep: int, seed: int) -> None:
         ka_set_state(self.ctx, n, n0, p, sweep, seed)
+
+    def set_state_async(self, n, n0, p, sweep: int, seed: int) -> None:
+        ka_set_state_async(self.ctx, n, n0, p, sweep, seed)
 
     def close(self) -> None:
         ka_destroy(self.ctx)

@@ -403,9 +403,14 @@ ka_status ka_get_state(ka_ctx* c, uint64_t* n, uint64_t* n0, uint64_t* p) {
   return KA_OK;
 }
 
-ka_status ka_set_state(ka_ctx* c, const uint64_t* n, const uint64_t* n0, const uint64_t* p,
-                       int64_t sweep, uint64_t seed) {
-  ka::NvtxRange nvtx_range("ka_set_state");
+}  // extern "C"
+
+namespace {
+
+// Queue the copies of a canonical-layout state onto the context's stream;
+// synchronises when sync.
+ka_status set_state_impl(ka_ctx* c, const uint64_t* n, const uint64_t* n0, const uint64_t* p,
+                         int64_t sweep, uint64_t seed, bool sync) {
   if (!c || !n || !n0 || !p || sweep < 0 || sweep >= ((int64_t)1 << 32)) return KA_EINVAL;
   DeviceGuard dg(c->device);
   const size_t bytes = (size_t)c->pl.P * c->pl.plane_elems() * sizeof(uint64_t);
@@ -414,13 +419,15 @@ ka_status ka_set_state(ka_ctx* c, const uint64_t* n, const uint64_t* n0, const u
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < 3 && !e; ++k) {
     if (c->pl.V > 1) {
+      // stream order keeps the next copy from overwriting the staging plane
+      // before the conversion has read it
       e = cudaMemcpyAsync(c->stage, src[k], bytes, cudaMemcpyHostToDevice, c->stream);
       if (!e) e = ka::launch_to_device(c->stage, dst[k], c->N, c->pl.P, c->pl.V, c->stream);
     } else {
       e = cudaMemcpyAsync(dst[k], src[k], bytes, cudaMemcpyHostToDevice, c->stream);
     }
   }
-  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (!e && sync) e = cudaStreamSynchronize(c->stream);
   if (e) return cuda_fail(c, e, "set_state");
   c->sweep = sweep;
   c->seed = seed;
@@ -428,6 +435,22 @@ ka_status ka_set_state(ka_ctx* c, const uint64_t* n, const uint64_t* n0, const u
   c->K = -1;
   c->initialized = true;
   return KA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ka_status ka_set_state(ka_ctx* c, const uint64_t* n, const uint64_t* n0, const uint64_t* p,
+                       int64_t sweep, uint64_t seed) {
+  ka::NvtxRange nvtx_range("ka_set_state");
+  return set_state_impl(c, n, n0, p, sweep, seed, true);
+}
+
+ka_status ka_set_state_async(ka_ctx* c, const uint64_t* n, const uint64_t* n0, const uint64_t* p,
+                             int64_t sweep, uint64_t seed) {
+  ka::NvtxRange nvtx_range("ka_set_state_async");
+  return set_state_impl(c, n, n0, p, sweep, seed, false);
 }
 
 ka_status ka_sync(ka_ctx* c) {

@@ -172,6 +172,37 @@ def test_sweeps_compose_and_checkpoint():
         assert (x == y).all()
 
 
+@pytest.mark.parametrize("replicas", [64, 256])
+def test_asynchronous_state_load(replicas):
+    # ka_set_state_async from page-locked memory on a side stream, then sweeps
+    # queued behind it: the same state as the synchronous load
+    kw = dict(topo=K.KA_CUBIC, d=3, L=16, m=3, replicas=replicas)
+    a = K.Simulation(**kw)
+    a.init(5, 0.75)
+    a.sweep(5)
+    snap = a.get_state()
+    a.sweep(7)
+    ref = a.get_state()
+    pinned = []
+    for x in snap:
+        t = torch.empty(x.shape, dtype=torch.int64, pin_memory=True)
+        t.numpy().view(np.uint64)[...] = x
+        pinned.append(t.numpy().view(np.uint64))
+    st = torch.cuda.Stream()
+    b = K.Simulation(stream=st, **kw)
+    b.set_state_async(*pinned, sweep=5, seed=5)
+    b.sweep(7)
+    K.ka_sync(b.ctx)
+    assert not b.ctx.inflight
+    got = b.get_state()
+    for x, y in zip(ref, got):
+        assert (x == y).all()
+    with pytest.raises(ValueError):
+        b.set_state_async(snap[0][:, ::2], snap[1], snap[2], sweep=0, seed=5)
+    a.close()
+    b.close()
+
+
 def test_errors_surface_as_status():
     sim = K.Simulation(topo=K.KA_CUBIC, d=2, L=8, m=1, replicas=64)
     with pytest.raises(K.KaError) as e:
