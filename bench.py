@@ -144,6 +144,13 @@ def oracle_sample(n_rep: int, sweeps: int, rho: float = RHOS[0]):
     return N_SITES * n_rep * sweeps / dt, dt
 
 
+def workload_config(world: int, sweeps: int) -> dict:
+    """The "config" of the cubic bench line (both arms)."""
+    return {"workload": WORKLOAD, "L": L, "d": D, "m": M, "replicas": R, "rho": list(RHOS),
+            "sweeps_per_step": sweeps, "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (576 MiB of state per GPU)"}
+
+
 def run_reference(args, rank: int) -> None:
     if rank != 0:
         return
@@ -166,7 +173,7 @@ def run_reference(args, rank: int) -> None:
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "L": L, "d": D, "m": M, "replicas": R, "rho": list(RHOS)},
+        "config": workload_config(args.gpus, args.sweeps),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -324,9 +331,7 @@ def run_native(args, rank: int, world: int) -> None:
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "L": L, "d": D, "m": M, "replicas": R,
-                       "rho": list(RHOS), "sweeps_per_step": S, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (576 MiB of state per GPU)"},
+            "config": workload_config(world, S),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_cubic_group", "peak_kind": peak_kind,
