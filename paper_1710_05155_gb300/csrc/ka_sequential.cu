@@ -14,11 +14,13 @@
 // its attempts 32 at a time, one per lane, with the result of the chain in
 // order.  An attempt reads n on its read set R = {i, j} and the neighbours
 // of i and of j, and writes n and p on W = {i, j}.  Attempts k and l
-// conflict when W_k meets R_l or W_l meets R_k: every attempt sets its lane
-// bit in a shared-memory stamp word of both sites of W, then ORs the stamps
-// over R (sites share a stamp modulo the table size when N is larger; a shared
-// stamp can only add conflicts), and a transpose by ballots adds the other
-// direction.  The warp applies the
+// conflict when W_k meets R_l or W_l meets R_k.  The neighbour relation is
+// symmetric (cubic lattices by construction, graphs are checked when the
+// context is made), so the two are the same condition: a site of W_k equals
+// a site of W_l or neighbours one.  Every attempt sets its lane bit in a
+// shared-memory stamp word of both sites of W, then ORs the stamps over R
+// (sites share a stamp modulo the table size when N is larger; a shared
+// stamp can only add conflicts).  The warp applies the
 // pending attempts in rounds: in each, every pending attempt that conflicts
 // with no earlier pending attempt (a set that always holds the earliest)
 // reads, decides and writes.  Such an attempt sees exactly the state the
@@ -180,11 +182,6 @@ __global__ void __launch_bounds__(32) k_sequential(const __grid_constant__ SeqAr
         stamp[j & hm] = 0;
       }
       __syncwarp();
-      // and the other way round (transpose of the warp's bit matrix)
-      for (int o = 0; o < 32; ++o) {
-        const uint32_t col = __ballot_sync(0xffffffffu, (conf >> o) & 1u);
-        if (lane == o) conf |= col;
-      }
       uint32_t pending = __ballot_sync(0xffffffffu, live);
       while (pending) {
         const bool ready = ((pending >> lane) & 1u) && !(conf & pending & earlier);
