@@ -95,7 +95,10 @@ typedef struct {
     int32_t m;           /* activation number, 0 <= m <= z - 1 (section 2.1) */
     int32_t replicas;    /* R, a positive multiple of 64 */
     uint64_t graph_seed; /* KA_RRG */
-    const int32_t *nbr;  /* KA_GRAPH: host array [N][z], copied at create; else NULL */
+    const int32_t *nbr;  /* KA_GRAPH: host array [N][z], copied at create (rows kept in
+                            ascending order); else NULL.  The rows must describe a simple
+                            undirected graph: v in row u iff u in row v, no self-loop, no
+                            repeated entry; ka_create returns KA_EINVAL otherwise */
     void *stream;        /* cudaStream_t for all work of the context; NULL = legacy default */
     int32_t device;      /* CUDA device ordinal */
     int32_t flags;       /* KA_FLAG_* */
