@@ -37,6 +37,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 D, L, M, R, SEED = 3, 128, 3, 256, 1
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy peak is the roofline's)
 RHOS = (0.80, 0.85, 0.88)
 N_SITES = L ** D
 WORDS = R // 64
@@ -334,6 +335,7 @@ def run_native(args, rank: int, world: int) -> None:
             "config": workload_config(world, S),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                          "kernel": "k_cubic_group", "peak_kind": peak_kind,
                          "avg_launch_us": 1000.0 * avg_launch_ms,
                          "avg_launch_us_isolated": 1000.0 * isolated_launch_ms,
@@ -347,6 +349,9 @@ def run_native(args, rank: int, world: int) -> None:
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
+            # a sweep attempts each of the N z / 2 bonds once per replica: z / 2 = d
+            # bond attempts per site-replica move
+            "bond_attempts_per_s": value * D,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
         }
