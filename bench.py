@@ -152,6 +152,39 @@ def workload_config(world: int, sweeps: int) -> dict:
             "l2": "inputs larger than L2 (576 MiB of state per GPU)"}
 
 
+def native_line(*, world, steps, warmup, sweeps, ms, value, achieved, peak, peak_kind, traffic,
+                avg_launch_ms, isolated_launch_ms, bytes_per_launch, cpu, e2e_value, h2d, d2h,
+                gpu_launches, clocks) -> dict:
+    """The JSON line of the native cubic arm from its measured numbers."""
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": workload_config(world, sweeps),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                     "kernel": "k_cubic_group", "peak_kind": peak_kind,
+                     "avg_launch_us": 1000.0 * avg_launch_ms,
+                     "avg_launch_us_isolated": 1000.0 * isolated_launch_ms,
+                     "bytes_per_launch": bytes_per_launch,
+                     # the DRAM bytes the kernel really moves per launch (the committed
+                     # ncu capture) over the same live launch time
+                     "dram_achieved": (traffic / (avg_launch_ms / 1000.0) / 1e9
+                                       if traffic else None),
+                     "dram_frac": (traffic / (avg_launch_ms / 1000.0) / 1e9 / peak
+                                   if traffic else None)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        # a sweep attempts each of the N z / 2 bonds once per replica: z / 2 = d
+        # bond attempts per site-replica move
+        "bond_attempts_per_s": value * D,
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+    }
+
+
 def run_reference(args, rank: int) -> None:
     if rank != 0:
         return
@@ -328,33 +361,13 @@ def run_native(args, rank: int, world: int) -> None:
             cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"L=128 d=3 m=3 rho=0.80, {n_rep} of 256 replicas, {sw} sweeps "
                              f"after an untimed init ({dt:.1f} s)"}
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": workload_config(world, S),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                         "kernel": "k_cubic_group", "peak_kind": peak_kind,
-                         "avg_launch_us": 1000.0 * avg_launch_ms,
-                         "avg_launch_us_isolated": 1000.0 * isolated_launch_ms,
-                         "bytes_per_launch": bytes_per_launch,
-                         # the DRAM bytes the kernel really moves per launch (the committed
-                         # ncu capture) over the same live launch time
-                         "dram_achieved": (traffic / (avg_launch_ms / 1000.0) / 1e9
-                                           if traffic else None),
-                         "dram_frac": (traffic / (avg_launch_ms / 1000.0) / 1e9 / peak
-                                       if traffic else None)},
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
-            # a sweep attempts each of the N z / 2 bonds once per replica: z / 2 = d
-            # bond attempts per site-replica move
-            "bond_attempts_per_s": value * D,
-            "gpu_launches": launches_per_step * args.steps,
-            "clocks": clk,
-        }
+        line = native_line(world=world, steps=args.steps, warmup=args.warmup, sweeps=S, ms=ms,
+                           value=value, achieved=achieved, peak=peak, peak_kind=peak_kind,
+                           traffic=traffic, avg_launch_ms=avg_launch_ms,
+                           isolated_launch_ms=isolated_launch_ms,
+                           bytes_per_launch=bytes_per_launch, cpu=cpu, e2e_value=e2e_value,
+                           h2d=h2d, d2h=d2h, gpu_launches=launches_per_step * args.steps,
+                           clocks=clk)
         print(json.dumps(line), flush=True)
     for sim in sims + e2e_sims:
         sim.close()
