@@ -144,3 +144,14 @@ def test_layered_graph_rejects(d, L, M):
     with pytest.raises(K.KaError) as e:
         K.ka_layered_graph(d, L, M, 1)
     assert e.value.status == K.KA_EINVAL
+
+
+def test_asynchronous_state_load_checks_its_arrays():
+    # rejected before the library is called: the copies read the caller's
+    # memory after the call returns, so no temporary copy may stand in
+    ctx = K.Ctx(0)
+    good = np.zeros((1, 64), np.uint64)
+    for bad in (np.zeros((1, 128), np.uint64)[:, ::2], np.zeros((1, 64), np.int64), [0] * 64):
+        with pytest.raises(ValueError):
+            K.ka_set_state_async(ctx, bad, good, good, 0, 1)
+    assert not ctx.inflight
