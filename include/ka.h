@@ -21,10 +21,17 @@
  * persistence bit of both sites.
  *
  * Random gates.  Philox4x32-10 (Salmon et al., SC'11), key = (seed low 32,
- * seed high 32).  The gate word of word w of bond b in class c at sweep t is
- * half (w mod 2) of the block at counter (t, c, b, w / 2); half 0 is
- * x0 | x1 << 32, half 1 is x2 | x3 << 32.  Bond b is the base site index on
- * cubic lattices and the edge id on graphs.
+ * seed high 32); a block at counter (c0, c1, c2, c3) has halves
+ * half 0 = x0 | x1 << 32 and half 1 = x2 | x3 << 32.  The gate word that
+ * replica word w of a bond uses at sweep t is:
+ *   - graphs (random regular and caller graphs): half (w mod 2) of the block
+ *     at counter (t, c, e, w / 2), c the bond's class and e its edge id;
+ *   - cubic lattices: classes pair up as (4g + 2b, 4g + 2b + 1), b in {0, 1},
+ *     g = 2 mu + p the group.  A bond of class c with base site i takes half
+ *     (c mod 2) of the block at counter (t, c - (c mod 2), i - (c mod 2) L^mu,
+ *     w): the bonds at pencil positions 4k + 2b and 4k + 2b + 1 of one pencil
+ *     share the block keyed by the base site of the first, and every word w
+ *     has its own block.
  *
  * Cubic schedule (d-dimensional periodic lattice, L % 4 == 0, site index
  * i = sum_k x_k L^k).  Class c = (2 mu + p) * 4 + a, for mu < d, p in {0, 1}
@@ -355,12 +362,15 @@ ka_status ka_batch_destroy(ka_batch *b);
  * n, n0, p: device arrays in the canonical layout [R/64][N] uint64 (the
  * layout of ka_get_state), read only.  counts: host int64 [R][4], written
  * as by ka_observe.  stream: cudaStream_t or NULL.  Synchronises the stream.
- * Returns KA_EINVAL when replicas is not a multiple of 64 or exceeds 4096.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All
- * calls share the one array, which keeps the last call's contents (each call
- * clears it first), so calls that overlap on the GPU -- concurrent streams
- * or host threads -- race and must be serialised by the caller. */
+ * Returns KA_EINVAL when replicas is not a multiple of 64 or exceeds 4096,
+ * or when stream belongs to another device than the current one (the array
+ * used is the current device's).  The first call on a device looks up the
+ * array's device address (with that device current, once, safely from any
+ * host thread).  Every call copies the counts to the host and synchronises
+ * the stream, so no call may be made while the stream is being captured.
+ * All calls share the one array, which keeps the last call's contents (each
+ * call clears it first), so calls that overlap on the GPU -- concurrent
+ * streams or host threads -- race and must be serialised by the caller. */
 ka_status ka_observe_static(const uint64_t *n, const uint64_t *n0, const uint64_t *p, int64_t N,
                             int32_t replicas, int64_t *counts, void *stream);
 
