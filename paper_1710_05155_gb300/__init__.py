@@ -186,14 +186,18 @@ def ka_layered_graph(d: int, L: int, M: int, graph_seed: int) -> np.ndarray:
 def ka_create(params: ka_params, keep=()) -> Ctx:
     h = C.c_void_p(0)
     _check(load().ka_create(C.byref(params), C.byref(h)), "ka_create")
-    return Ctx(h.value, keep)
+    ctx = Ctx(h.value, keep)
+    ctx.info = ka_info(ctx)
+    return ctx
 
 
 def ka_create_in(params: ka_params, device_ptr: int, nbytes: int, keep=()) -> Ctx:
     h = C.c_void_p(0)
     _check(load().ka_create_in(C.byref(params), C.c_void_p(device_ptr), nbytes, C.byref(h)),
            "ka_create_in")
-    return Ctx(h.value, keep)
+    ctx = Ctx(h.value, keep)
+    ctx.info = ka_info(ctx)
+    return ctx
 
 
 def ka_init(ctx: Ctx, seed: int, rho: float) -> None:
@@ -253,8 +257,20 @@ def ka_get_state(ctx: Ctx):
     return n, n0, p
 
 
+def _check_state_sizes(ctx: Ctx, arrays, where: str) -> None:
+    """Each state array must hold exactly R/64 * N words: the library copies
+    that many from every host pointer."""
+    info = ctx.info if ctx.info is not None else ka_info(ctx)
+    need = int(info["words"]) * int(info["N"])
+    for x in arrays:
+        if x.size != need:
+            raise ValueError(f"{where}: every array must hold R/64 * N = {need} words "
+                             f"(shape (R/64, N)), got {x.size}")
+
+
 def ka_set_state(ctx: Ctx, n, n0, p, sweep: int, seed: int) -> None:
     n, n0, p = (np.ascontiguousarray(x, np.uint64) for x in (n, n0, p))
+    _check_state_sizes(ctx, (n, n0, p), "ka_set_state")
     _check(load().ka_set_state(ctx.handle, _ptr(n), _ptr(n0), _ptr(p), sweep, seed),
            "ka_set_state", ctx)
     ctx.inflight.clear()
@@ -268,6 +284,7 @@ def ka_set_state_async(ctx: Ctx, n, n0, p, sweep: int, seed: int) -> None:
     for x in (n, n0, p):
         if not (isinstance(x, np.ndarray) and x.dtype == np.uint64 and x.flags.c_contiguous):
             raise ValueError("ka_set_state_async needs C-contiguous uint64 arrays")
+    _check_state_sizes(ctx, (n, n0, p), "ka_set_state_async")
     _check(load().ka_set_state_async(ctx.handle, _ptr(n), _ptr(n0), _ptr(p), sweep, seed),
            "ka_set_state_async", ctx)
     ctx.inflight.append((n, n0, p))

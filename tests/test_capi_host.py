@@ -150,8 +150,25 @@ def test_asynchronous_state_load_checks_its_arrays():
     # rejected before the library is called: the copies read the caller's
     # memory after the call returns, so no temporary copy may stand in
     ctx = K.Ctx(0)
+    ctx.info = {"words": 1, "N": 64}
     good = np.zeros((1, 64), np.uint64)
     for bad in (np.zeros((1, 128), np.uint64)[:, ::2], np.zeros((1, 64), np.int64), [0] * 64):
         with pytest.raises(ValueError):
             K.ka_set_state_async(ctx, bad, good, good, 0, 1)
+    assert not ctx.inflight
+
+
+@pytest.mark.parametrize("shape", [(1, 63), (2, 64), (0,), (1, 65)])
+def test_state_load_checks_sizes(shape):
+    # the library copies R/64 * N words from each host pointer: a shorter array
+    # would be read past its end, a longer one silently truncated
+    ctx = K.Ctx(0)
+    ctx.info = {"words": 1, "N": 64}
+    good = np.zeros((1, 64), np.uint64)
+    bad = np.zeros(shape, np.uint64)
+    for args in ((bad, good, good), (good, bad, good), (good, good, bad)):
+        with pytest.raises(ValueError):
+            K.ka_set_state_async(ctx, *args, 0, 1)
+        with pytest.raises(ValueError):
+            K.ka_set_state(ctx, *args, 0, 1)
     assert not ctx.inflight
