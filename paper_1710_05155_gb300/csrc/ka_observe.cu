@@ -15,6 +15,7 @@
 // bit-sliced form through warp shuffles, the warp total is turned into one
 // integer per replica, and blocks accumulate in shared memory before one
 // 64-bit atomic per counter goes to global memory.
+#include <mutex>
 #include "ka_internal.cuh"
 
 namespace ka {
@@ -155,24 +156,34 @@ static __device__ __align__(256) unsigned long long g_static_counts[kStaticMaxRe
 
 namespace {
 constexpr int kMaxDevices = 64;
-unsigned long long* g_static_ptr[kMaxDevices] = {};  // device address of the array, per device
+
+// The array's device address on one device, looked up once: std::call_once
+// orders the lookup before every use from any host thread.
+struct StaticSlot {
+  std::once_flag once;
+  cudaError_t err = cudaSuccess;
+  unsigned long long* ptr = nullptr;
+};
+StaticSlot g_static_slot[kMaxDevices];
 }  // namespace
 
 // Device address of the array on the current device.  In host code the
 // symbol itself is only a host-side stand-in, so its address is looked up
-// once per device (with that device current) and cached.
+// (with that device current) by the first call on each device and cached;
+// a failed lookup is returned to every later call on that device.
 cudaError_t static_counts_ptr(unsigned long long** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (!g_static_ptr[dev]) {
+  StaticSlot& s = g_static_slot[dev];
+  std::call_once(s.once, [&s] {
     void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_static_counts);
-    if (e != cudaSuccess) return e;
-    g_static_ptr[dev] = (unsigned long long*)ptr;
-  }
-  *out = g_static_ptr[dev];
+    s.err = cudaGetSymbolAddress(&ptr, g_static_counts);
+    s.ptr = (unsigned long long*)ptr;
+  });
+  if (s.err != cudaSuccess) return s.err;
+  *out = s.ptr;
   return cudaSuccess;
 }
 
@@ -185,6 +196,14 @@ extern "C" ka_status ka_observe_static(const uint64_t* n, const uint64_t* n0, co
       replicas > ka::kStaticMaxReplicas)
     return KA_EINVAL;
   const cudaStream_t st = (cudaStream_t)stream;
+  if (st) {
+    // the array whose address is used is the current device's: the stream
+    // must belong to that device
+    int cur = 0, sdev = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess || cudaStreamGetDevice(st, &sdev) != cudaSuccess)
+      return KA_ECUDA;
+    if (sdev != cur) return KA_EINVAL;
+  }
   unsigned long long* scratch = nullptr;
   cudaError_t e = ka::static_counts_ptr(&scratch);
   if (e != cudaSuccess) return KA_ECUDA;
