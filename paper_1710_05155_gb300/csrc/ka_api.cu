@@ -4,6 +4,7 @@
 // planes n, n0, p; the per-replica observable counters; the init scratch;
 // and, on the edge-gather path, the neighbour list and the class-ordered
 // bond arrays.  All work is issued on the context stream in call order.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -19,11 +20,12 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t n, n0, p, stage, counts, hist, pre_key, pre_idx, krem, unresolved, nbr, bu, bv, bid, total;
+  size_t n, n0, p, stage, counts, hist, pre_key, pre_idx, krem, unresolved, err, nbr, bu, bv, bid,
+      total;
 };
 
 struct Shape {
-  int topo, d, L, z, m, R, W, V, P;
+  int topo, d, L, z, m, R, W, V, P, xs;
   int64_t N, E;
   bool pencil;
 };
@@ -66,9 +68,17 @@ const char* check_params(const ka_params* p, Shape& s) {
   }
   if (s.m < 0 || s.m > s.z - 1) return "m must be in [0, z-1]";
   // words per site and plane: a whole 32-byte sector per site when 4 words
-  // fit (the pencil kernel stages sectors; the edge-gather kernel's random
-  // accesses move whole sectors anyway)
+  // fit (the edge-gather kernel's random accesses move whole sectors anyway).
+  // Cubic lattices of dimension >= 2 on the pencil kernels keep one word per
+  // site and plane in split-row order: a plane's n and p (16 bytes per site)
+  // then stay resident in the L2 across the sweeps of that plane, and a
+  // group's active sites are whole sectors.
   if (s.W % 4 == 0) s.V = 4;
+  s.xs = 0;
+  if (s.topo == KA_CUBIC && s.pencil && s.d >= 2) {
+    s.V = 1;
+    s.xs = ka::split_side(s.d, s.L);
+  }
   s.P = s.W / s.V;
   return nullptr;
 }
@@ -85,13 +95,14 @@ Layout layout_of(const Shape& s) {
   l.n = take(plane);
   l.n0 = take(plane);
   l.p = take(plane);
-  l.stage = (s.V > 1) ? take(plane) : 0;  // layout conversion of get/set_state
+  l.stage = (s.V > 1 || s.xs) ? take(plane) : 0;  // layout conversion of get/set_state
   l.counts = take((size_t)s.R * 4 * sizeof(unsigned long long));
   l.hist = take((size_t)s.R * 256 * sizeof(uint32_t));
   l.pre_key = take((size_t)s.R * sizeof(uint64_t));
   l.pre_idx = take((size_t)s.R * sizeof(uint32_t));
   l.krem = take((size_t)s.R * sizeof(int64_t));
   l.unresolved = take(sizeof(int32_t));
+  l.err = take(sizeof(int32_t));
   if (!s.pencil) {
     l.nbr = take((size_t)s.N * s.z * sizeof(int32_t));
     l.bu = take((size_t)s.E * sizeof(int32_t));
@@ -150,8 +161,10 @@ ka_status create_common(const ka_params* params, void* buf, size_t bytes, bool o
   c->pl.W = s.W;
   c->pl.V = s.V;
   c->pl.P = s.P;
+  c->pl.xs = s.xs;
+  c->err_dev = (int*)(base + l.err);
   c->counts_dev = (unsigned long long*)(base + l.counts);
-  c->stage = (s.V > 1) ? (uint64_t*)(base + l.stage) : nullptr;
+  c->stage = (s.V > 1 || s.xs) ? (uint64_t*)(base + l.stage) : nullptr;
   c->is.hist = (uint32_t*)(base + l.hist);
   c->is.pre_key = (uint64_t*)(base + l.pre_key);
   c->is.pre_idx = (uint32_t*)(base + l.pre_idx);
@@ -160,6 +173,14 @@ ka_status create_common(const ka_params* params, void* buf, size_t bytes, bool o
   c->is.cand = c->stage ? (uint32_t*)c->stage : nullptr;  // idle during init
   c->is.cand_bytes = c->stage ? (size_t)s.N * s.W * sizeof(uint64_t) : 0;
 
+  {
+    const cudaError_t ez = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
+    if (ez || cudaStreamSynchronize(c->stream)) {
+      if (owns) cudaFree(buf);
+      delete c;
+      return KA_ECUDA;
+    }
+  }
   std::string msg;
   if (s.topo == KA_CUBIC) {
     c->nclass = (s.d == 1) ? 4 : 8 * s.d;
@@ -228,6 +249,24 @@ ka_status drain_profile(ka_ctx* c) {
     c->prof_launches++;
   }
   c->ev_used = 0;
+  return KA_OK;
+}
+
+// Read (and clear) the device error word of the bounded waits; synchronises
+// the context stream.  KA_ETIMEOUT when a wait ran out since the last check.
+ka_status check_device_error(ka_ctx* c) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_fail(c, e, "sync");
+  if (h) {
+    e = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "sync");
+    return fail(c, KA_ETIMEOUT,
+                std::string("a bounded device wait ran out (code ") +
+                    std::to_string(h) + "); the state of this context is not valid");
+  }
   return KA_OK;
 }
 
@@ -317,7 +356,27 @@ ka_status ka_sweep(ka_ctx* c, int64_t n) {
   if (n == 0) return KA_OK;
   DeviceGuard dg(c->device);
   cudaError_t e = cudaSuccess;
-  if (c->pencil) {
+  if (c->pencil && ka::stream_supported(c->d, c->L)) {
+    // plane-outer order keeps the planes of one launch resident in the L2
+    // across sweeps
+    const int nq = ka::stream_planes_per_launch(c->L, c->pl.P);
+    for (int q0 = 0; q0 < c->pl.P && !e; q0 += nq) {
+      const int cnt = std::min(nq, c->pl.P - q0);
+      for (int64_t s = 0; s < n && !e; ++s)
+        for (int mu = 0; mu < 3 && !e; ++mu)
+          for (int par = 0; par < 2 && !e; ++par) {
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (c->prof) {
+              e0 = next_event(c);
+              e1 = next_event(c);
+              if (e0) cudaEventRecord(e0, c->stream);
+            }
+            e = ka::launch_stream_group(c->pl, q0, cnt, c->L, c->m, mu, par,
+                                        (uint32_t)(c->sweep + s), c->rk, c->stream);
+            if (e1) cudaEventRecord(e1, c->stream);
+          }
+    }
+  } else if (c->pencil) {
     const ka::CubicShape sh{c->d, c->L, c->m};
     const int npar = (c->d == 1) ? 1 : 2;
     // plane-outer order keeps one plane's n and p resident in L2 across sweeps
@@ -373,8 +432,8 @@ ka_status ka_observe(ka_ctx* c, int64_t* sweep_out, int64_t* counts) {
   cudaError_t e = ka::launch_observe(c->pl, c->R, c->counts_dev, c->stream);
   if (!e) e = cudaMemcpyAsync(counts, c->counts_dev, (size_t)c->R * 4 * sizeof(int64_t),
                               cudaMemcpyDeviceToHost, c->stream);
-  if (!e) e = cudaStreamSynchronize(c->stream);
   if (e) return cuda_fail(c, e, "observe");
+  if (ka_status st = check_device_error(c)) return st;
   if (sweep_out) *sweep_out = c->sweep;
   return KA_OK;
 }
@@ -390,17 +449,16 @@ ka_status ka_get_state(ka_ctx* c, uint64_t* n, uint64_t* n0, uint64_t* p) {
   for (int k = 0; k < 3 && !e; ++k) {
     if (!dst[k]) continue;
     const uint64_t* from = src[k];
-    if (c->pl.V > 1) {
-      e = ka::launch_to_canonical(src[k], c->stage, c->N, c->pl.P, c->pl.V, c->stream);
+    if (c->stage) {
+      e = ka::launch_to_canonical(src[k], c->stage, c->N, c->pl.P, c->pl.V, c->pl.xs, c->stream);
       from = c->stage;
     }
     // stream order keeps the next conversion from overwriting the staging
     // plane before this copy has read it
     if (!e) e = cudaMemcpyAsync(dst[k], from, bytes, cudaMemcpyDeviceToHost, c->stream);
   }
-  if (!e) e = cudaStreamSynchronize(c->stream);
   if (e) return cuda_fail(c, e, "get_state");
-  return KA_OK;
+  return check_device_error(c);
 }
 
 }  // extern "C"
@@ -418,11 +476,12 @@ ka_status set_state_impl(ka_ctx* c, const uint64_t* n, const uint64_t* n0, const
   uint64_t* dst[3] = {c->pl.n, c->pl.n0, c->pl.p};
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < 3 && !e; ++k) {
-    if (c->pl.V > 1) {
+    if (c->stage) {
       // stream order keeps the next copy from overwriting the staging plane
       // before the conversion has read it
       e = cudaMemcpyAsync(c->stage, src[k], bytes, cudaMemcpyHostToDevice, c->stream);
-      if (!e) e = ka::launch_to_device(c->stage, dst[k], c->N, c->pl.P, c->pl.V, c->stream);
+      if (!e)
+        e = ka::launch_to_device(c->stage, dst[k], c->N, c->pl.P, c->pl.V, c->pl.xs, c->stream);
     } else {
       e = cudaMemcpyAsync(dst[k], src[k], bytes, cudaMemcpyHostToDevice, c->stream);
     }
@@ -458,7 +517,7 @@ ka_status ka_sync(ka_ctx* c) {
   DeviceGuard dg(c->device);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e) return cuda_fail(c, e, "sync");
-  return KA_OK;
+  return check_device_error(c);
 }
 
 ka_status ka_info(const ka_ctx* c, ka_info_t* out) {
@@ -549,6 +608,7 @@ ka_status ka_destroy(ka_ctx* c) {
   ka_status st = KA_OK;
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e) st = KA_ECUDA;
+  else st = check_device_error(c);
   for (cudaEvent_t ev : c->ev) cudaEventDestroy(ev);
   if (c->owns && c->buf) cudaFree(c->buf);
   delete c;

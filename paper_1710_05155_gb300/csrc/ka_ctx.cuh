@@ -19,6 +19,7 @@ struct ka_ctx {
   ka::Planes pl{};
   ka::InitScratch is{};
   unsigned long long* counts_dev = nullptr;
+  int* err_dev = nullptr;  // device error word of bounded device waits (0 = none)
   uint64_t* stage = nullptr;
   ka::GraphDev g{};
   ka::Topology host;  // class offsets (graphs) and tables for inspection

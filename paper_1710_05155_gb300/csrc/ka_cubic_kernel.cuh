@@ -251,25 +251,50 @@ struct PencilMap {
   }
 };
 
-// Per-pencil table of a CTA, built once in shared memory: the site index of
-// position 0 and the signed offsets to the perpendicular neighbours (with
-// the periodic wrap folded in).
+// Per-pencil table of a CTA, built once in shared memory: the position of
+// the pencil's site 0 in the plane, the signed offsets to the perpendicular
+// neighbours (with the periodic wrap folded in), both in the plane's site
+// order, and the canonical index of site 0 (the gate counters).
 template <int D>
 struct PencilInfo {
   uint32_t base;
+  uint32_t cbase;
   int32_t nb[2 * (D - 1) > 0 ? 2 * (D - 1) : 1];
 };
+
+// offset of x within its row in the split-row order of a plane (d >= 2):
+// even x first, then odd x
+__device__ __forceinline__ int32_t xoff(int x, int L) { return (x & 1) * (L >> 1) + (x >> 1); }
 
 template <int D, int V, bool X>
 __device__ __forceinline__ void build_info(const GroupArgs& a, const PencilMap<D, V, X>& pm, int j,
                                            PencilInfo<D>& out) {
   int y[3] = {0, 0, 0};
-  out.base = pm.coords(a, j, y);
+  out.cbase = pm.coords(a, j, y);
+  out.base = out.cbase;
 #pragma unroll
   for (int k = 0; k < D - 1; ++k) {
     const int32_t s = (int32_t)a.st[a.pd[k]];
     out.nb[2 * k] = (y[k] == a.L - 1) ? -(a.L - 1) * s : s;
     out.nb[2 * k + 1] = (y[k] == 0) ? (a.L - 1) * s : -s;
+  }
+  if constexpr (D >= 2 && !X) {
+    // the pencil sits at x = y[0] (dimension 0 is perpendicular); its x
+    // neighbours are in the other half of the row
+    const int L = a.L, x = y[0];
+    out.base = out.cbase - (uint32_t)x + (uint32_t)xoff(x, L);
+    out.nb[0] = xoff(x == L - 1 ? 0 : x + 1, L) - xoff(x, L);
+    out.nb[1] = xoff(x == 0 ? L - 1 : x - 1, L) - xoff(x, L);
+  }
+}
+
+// position in the plane of site t of a pencil whose site 0 is at `base`
+template <int D, bool X>
+__device__ __forceinline__ uint32_t pencil_pos(uint32_t base, int t, uint32_t smu, int L) {
+  if constexpr (X && D >= 2) {
+    return base + (uint32_t)xoff(t, L);  // rows in split-row order
+  } else {
+    return base + (uint32_t)t * smu;
   }
 }
 
@@ -399,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, KA_CUBIC_MIN_BLOCKS)
           t = f;
           hh = h;
         }
-        const uint32_t site = base + (uint32_t)t * smu;
+        const uint32_t site = pencil_pos<D, X>(base, t, smu, L);
         const int e = j * PS + slot(t);
         cp_async8(splane(b, 0, hh) + e, a.n + (size_t)site * V + hh);
         cp_async8_hint(splane(b, 1, hh) + e, a.p + (size_t)site * V + hh, pol_p);
@@ -481,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, KA_CUBIC_MIN_BLOCKS)
       if (valid) {
         const int prev = gj * S + (seg == 0 ? S - 1 : seg - 1);
         const int next = gj * S + (seg == S - 1 ? 0 : seg + 1);
-        const uint32_t s0 = info[b][j].base + (uint32_t)(4 * seg) * smu;
+        const uint32_t s0 = info[b][j].cbase + (uint32_t)(4 * seg) * smu;
         // gate blocks: classes (0, 1) share one, (2, 3) the other; they do not
         // depend on the state, so start them first
         const uint4 g01 = philox(make_uint4(a.t, a.cls0, s0, word), a.rk);
@@ -575,7 +600,7 @@ __global__ void __launch_bounds__(kThreads, KA_CUBIC_MIN_BLOCKS)
           t = f;
           hh = h;
         }
-        const uint32_t site = base + (uint32_t)t * smu;
+        const uint32_t site = pencil_pos<D, X>(base, t, smu, L);
         const int e = j * PS + slot(t);
         a.n[(size_t)site * V + hh] = splane(b, 0, hh)[e];
         st_hint(a.p + (size_t)site * V + hh, splane(b, 1, hh)[e], pol_p);

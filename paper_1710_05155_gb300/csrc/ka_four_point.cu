@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) k_phi(Planes pl, Geometry g, const Vec* _
   for (int k = 0; k < spt; ++k) {
     const size_t e = e0 + (size_t)k * blockDim.x;
     if (e >= E) break;
-    const int64_t i = (int64_t)(e / V);
+    const int64_t i = canon_site(pl.xs, (int64_t)(e / V));  // the site held at element e
     const int h = (int)(e % V);
     const uint64_t qi = n[e] & n0[e];
     if (qi == 0) continue;
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) k_phi(Planes pl, Geometry g, const Vec* _
     coords(g, i, x);
     for (int t = v0; t < v1; ++t) {
       const int64_t j = shifted(g, x, vec[t]);
-      const size_t f = (size_t)j * V + h;
+      const size_t f = (size_t)dev_site(pl.xs, j) * V + h;
       ripple_add(c, qi & n[f] & n0[f]);
     }
   }
@@ -159,7 +159,7 @@ __global__ void k_site_counts(Planes pl, uint32_t* M) {
   for (int q = 0; q < pl.P; ++q)
 #pragma unroll
     for (int h = 0; h < V; ++h) {
-      const size_t e = (size_t)q * E + (size_t)i * V + h;
+      const size_t e = (size_t)q * E + (size_t)dev_site(pl.xs, i) * V + h;
       m += (uint32_t)__popcll(pl.n[e] & pl.n0[e]);
     }
   M[i] = m;

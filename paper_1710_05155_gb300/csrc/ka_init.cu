@@ -213,13 +213,13 @@ __global__ void k_init_rank(int64_t* krem, int R, int64_t K) {
   if (r < R) krem[r] = K;
 }
 
-// one thread per (site, word of a plane element): write n, n0, p
+// one thread per (site position, word of a plane element): write n, n0, p
 template <int V>
 __global__ void __launch_bounds__(256) k_init_mark(const InitArgs a, Planes pl) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int q = blockIdx.y;
   if (e >= a.N * V) return;
-  const int64_t i = e / V;
+  const int64_t i = canon_site(pl.xs, e / V);  // canonical site held at this position
   const int w = q * V + (int)(e % V);  // word index, replicas 64w .. 64w+63
   uint64_t word = 0;
   for (int j = 0; j < 32; ++j) {

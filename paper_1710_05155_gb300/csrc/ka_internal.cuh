@@ -103,10 +103,30 @@ struct Planes {
   uint64_t* p;
   int64_t N;
   int W;  // words per site (R / 64)
-  int V;  // words per site per plane (1 or 2)
+  int V;  // words per site per plane (1, 2 or 4)
   int P;  // planes (W / V)
+  int xs; // side L of the split-row site order (below), or 0: sites in index order
   KA_HD size_t plane_elems() const { return (size_t)N * V; }
 };
+
+// Site order of a plane.  Cubic lattices of dimension d >= 2 on the pencil
+// kernels store every row along x (L sites, L even) as its L/2 even-x sites
+// followed by its L/2 odd-x sites (xs = L), so that the sites a group with
+// mu > 0 updates in a row form one contiguous half-row; every other plane
+// keeps sites in index order (xs = 0).  Position of canonical site i:
+KA_HD int64_t dev_site(int xs, int64_t i) {
+  if (!xs) return i;
+  const int64_t x = i % xs;
+  return i - x + (x & 1) * (xs >> 1) + (x >> 1);
+}
+// and the canonical site at position q
+KA_HD int64_t canon_site(int xs, int64_t q) {
+  if (!xs) return q;
+  const int64_t r = q % xs, h = xs >> 1;
+  return q - r + (r < h ? 2 * r : 2 * (r - h) + 1);
+}
+// split-row order used by a cubic pencil context of dimension d and side L
+KA_HD int split_side(int d, int L) { return d >= 2 ? L : 0; }
 
 // Warps per CTA of the cubic pencil kernel: a tile holds kCubicWarps / V
 // active pencils (one warp per pencil-word in the compute phase).
@@ -197,11 +217,20 @@ struct InitScratch {
 cudaError_t launch_init(const Planes& pl, const InitScratch& s, int R, int64_t K,
                         const RoundKeys& rk, cudaStream_t st);
 
-// canonical [W][N] <-> device [P][N][V]
+// canonical [W][N] <-> device [P][N][V] (sites in the plane order of xs)
 cudaError_t launch_to_device(const uint64_t* canonical, uint64_t* device_layout, int64_t N, int P,
-                             int V, cudaStream_t st);
+                             int V, int xs, cudaStream_t st);
 cudaError_t launch_to_canonical(const uint64_t* device_layout, uint64_t* canonical, int64_t N,
-                                int P, int V, cudaStream_t st);
+                                int P, int V, int xs, cudaStream_t st);
+
+// Group kernels of three-dimensional lattices (ka_cubic_stream.cu): one-word
+// planes in split-row order, L in {32, 64, 128}.
+bool stream_supported(int d, int L);
+// planes one launch of these kernels takes
+int stream_planes_per_launch(int L, int P);
+// Group (mu, par) of sweep t on planes q0 .. q0 + nq - 1.
+cudaError_t launch_stream_group(const Planes& pl, int q0, int nq, int L, int m, int mu, int par,
+                                uint32_t t, const RoundKeys& rk, cudaStream_t st);
 
 cudaError_t launch_observe(const Planes& pl, int R, unsigned long long* counts_dev,
                            cudaStream_t st);

@@ -1,45 +1,46 @@
 // ka_layout.cu -- conversion between the canonical state layout of the ABI
 // ([W][N] uint64, word-plane major) and the device layout ([P][N][V], word w
-// of site i in plane w / V at element i * V + w % V).  With V = 1 both
-// layouts coincide.
+// of site i in plane w / V at element dev_site(xs, i) * V + w % V).  With
+// V = 1 and xs = 0 both layouts coincide.
 #include "ka_internal.cuh"
 
 namespace ka {
 namespace {
 
-// canonical -> device, one thread per (plane, site, word)
+// canonical -> device, one thread per (plane, site position, word)
 __global__ void k_to_device(const uint64_t* __restrict__ src, uint64_t* __restrict__ dst,
-                            int64_t N, int P, int V) {
+                            int64_t N, int P, int V, int xs) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // device element
   if (e >= (int64_t)P * N * V) return;
   const int64_t q = e / (N * V), r = e - q * N * V;
-  const int64_t i = r / V, h = r - i * V;
-  dst[e] = src[(q * V + h) * N + i];
+  const int64_t pos = r / V, h = r - pos * V;
+  dst[e] = src[(q * V + h) * N + canon_site(xs, pos)];
 }
 
 // device -> canonical
 __global__ void k_to_canonical(const uint64_t* __restrict__ src, uint64_t* __restrict__ dst,
-                               int64_t N, int P, int V) {
+                               int64_t N, int P, int V, int xs) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)P * N * V) return;
   const int64_t q = e / (N * V), r = e - q * N * V;
-  const int64_t i = r / V, h = r - i * V;
-  dst[(q * V + h) * N + i] = src[e];
+  const int64_t pos = r / V, h = r - pos * V;
+  dst[(q * V + h) * N + canon_site(xs, pos)] = src[e];
 }
 
 }  // namespace
 
 cudaError_t launch_to_device(const uint64_t* canonical, uint64_t* device_layout, int64_t N, int P,
-                             int V, cudaStream_t st) {
+                             int V, int xs, cudaStream_t st) {
   const int64_t n = (int64_t)P * N * V;
-  k_to_device<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(canonical, device_layout, N, P, V);
+  k_to_device<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(canonical, device_layout, N, P, V, xs);
   return cudaGetLastError();
 }
 
 cudaError_t launch_to_canonical(const uint64_t* device_layout, uint64_t* canonical, int64_t N,
-                                int P, int V, cudaStream_t st) {
+                                int P, int V, int xs, cudaStream_t st) {
   const int64_t n = (int64_t)P * N * V;
-  k_to_canonical<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(device_layout, canonical, N, P, V);
+  k_to_canonical<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(device_layout, canonical, N, P, V,
+                                                               xs);
   return cudaGetLastError();
 }
 

@@ -46,6 +46,7 @@ struct SeqArgs {
   const int32_t* nbr;  // [N][z], or null: periodic cubic lattice from coordinates
   int64_t N;
   int z, d, L, V;
+  int xs;  // split-row order of the planes (0: index order)
   size_t plane_elems;
   uint32_t t0;
   int nsweeps;
@@ -132,15 +133,19 @@ __global__ void __launch_bounds__(32) k_sequential(const __grid_constant__ SeqAr
   uint64_t* p = gp;
   int64_t st = a.V;
   if constexpr (SMEM) {
+    // shared memory holds the word's planes in site index order
     for (int64_t i = lane; i < a.N; i += 32) {
-      sm[i] = gn[i * a.V];
-      sm[a.N + i] = gp[i * a.V];
+      const int64_t g = dev_site(a.xs, i) * a.V;
+      sm[i] = gn[g];
+      sm[a.N + i] = gp[g];
     }
     __syncwarp();
     n = sm;
     p = sm + a.N;
     st = 1;
   }
+  // element of site i in n and p
+  auto at = [&](uint32_t i) -> int64_t { return SMEM ? (int64_t)i : dev_site(a.xs, i) * st; };
   uint32_t* stamp = reinterpret_cast<uint32_t*>(sm + (SMEM ? 2 * a.N : 0));
   const uint32_t hm = a.hmask;
   for (uint32_t b = lane; b <= hm; b += 32) stamp[b] = 0;
@@ -186,22 +191,22 @@ __global__ void __launch_bounds__(32) k_sequential(const __grid_constant__ SeqAr
       while (pending) {
         const bool ready = ((pending >> lane) & 1u) && !(conf & pending & earlier);
         if (ready) {
-          const uint64_t vi = n[(int64_t)i * st], vj = n[(int64_t)j * st];
+          const uint64_t vi = n[at(i)], vj = n[at(j)];
           uint64_t ci2 = 0, ci1 = 0, ci0 = 0, cj2 = 0, cj1 = 0, cj0 = 0;
 #pragma unroll
           for (int slot = 0; slot < 8; ++slot) {
             if (slot >= a.z) break;
-            if (ni_[slot] != j) add3(ci2, ci1, ci0, n[(int64_t)ni_[slot] * st]);
-            if (nj_[slot] != i) add3(cj2, cj1, cj0, n[(int64_t)nj_[slot] * st]);
+            if (ni_[slot] != j) add3(ci2, ci1, ci0, n[at(ni_[slot])]);
+            if (nj_[slot] != i) add3(cj2, cj1, cj0, n[at(nj_[slot])]);
           }
           // at most m occupied among the other neighbours of i and of j
           const uint64_t ok = le3<M>(ci2, ci1, ci0) & le3<M>(cj2, cj1, cj0);
           const uint64_t sw = (vi ^ vj) & ok;
           if (sw) {
-            n[(int64_t)i * st] = vi ^ sw;
-            n[(int64_t)j * st] = vj ^ sw;
-            p[(int64_t)i * st] &= ~sw;
-            p[(int64_t)j * st] &= ~sw;
+            n[at(i)] = vi ^ sw;
+            n[at(j)] = vj ^ sw;
+            p[at(i)] &= ~sw;
+            p[at(j)] &= ~sw;
           }
         }
         pending &= ~__ballot_sync(0xffffffffu, ready);
@@ -212,8 +217,9 @@ __global__ void __launch_bounds__(32) k_sequential(const __grid_constant__ SeqAr
   if constexpr (SMEM) {
     __syncwarp();
     for (int64_t i = lane; i < a.N; i += 32) {
-      gn[i * a.V] = sm[i];
-      gp[i * a.V] = sm[a.N + i];
+      const int64_t g = dev_site(a.xs, i) * a.V;
+      gn[g] = sm[i];
+      gp[g] = sm[a.N + i];
     }
   }
 }
@@ -278,6 +284,7 @@ extern "C" ka_status ka_sweep_sequential(ka_ctx* c, int64_t nsweeps) {
   a.d = c->d;
   a.L = c->L;
   a.V = c->pl.V;
+  a.xs = c->pl.xs;
   a.plane_elems = c->pl.plane_elems();
   a.rk = c->rk;
   const unsigned words = (unsigned)(c->R / 64);

@@ -269,12 +269,13 @@ def test_large_rrg_prefix():
 
 
 def test_large_cubic_two_planes_sampled_words():
-    """d=3, L=128, 512 replicas (two planes of four words): the last word of each
-    plane against the oracle on those 64 replicas, after two sweeps."""
+    """d=3, L=128, 512 replicas (eight one-word planes, four launches of two
+    planes per group): words 3 and 7 against the oracle on their 64 replicas,
+    after two sweeps."""
     L, R, seed, rho = 128, 512, 3, 0.85
     topo = O.cubic(3, L)
     sim = K.Simulation(topo=K.KA_CUBIC, d=3, L=L, m=3, replicas=R)
-    assert sim.info["planes"] == 2 and sim.info["plane_words"] == 4
+    assert sim.info["planes"] == 8 and sim.info["plane_words"] == 1
     sim.init(seed, rho)
     sim.sweep(2)
     n, _, p = sim.get_state()
@@ -304,10 +305,12 @@ def test_large_rrg_four_word_planes_sampled_word():
 
 
 @pytest.mark.parametrize("kw,rho", [
-    (dict(topo=K.KA_CUBIC, d=3, L=48, m=3, replicas=128), 0.3),   # two-word planes: candidate lists
+    (dict(topo=K.KA_CUBIC, d=3, L=48, m=3, replicas=128), 0.3),   # candidate lists, split rows
     (dict(topo=K.KA_CUBIC, d=3, L=48, m=3, replicas=128), 0.85),
-    (dict(topo=K.KA_CUBIC, d=3, L=64, m=3, replicas=256), 0.5),   # four-word planes
-    (dict(topo=K.KA_CUBIC, d=3, L=48, m=3, replicas=64), 0.6),    # one-word planes: full scans
+    (dict(topo=K.KA_CUBIC, d=3, L=64, m=3, replicas=256), 0.5),   # four one-word planes
+    (dict(topo=K.KA_CUBIC, d=3, L=48, m=3, replicas=64), 0.6),
+    (dict(topo=K.KA_CUBIC, d=1, L=4096, m=1, replicas=256), 0.6),  # index order, four-word planes
+    (dict(topo=K.KA_RRG, N=1 << 17, z=4, m=2, replicas=64, graph_seed=2), 0.7),  # full scans
 ])
 def test_initial_state_of_larger_lattices(kw, rho):
     """The initial state (exactly K particles per replica, the K smallest
@@ -315,7 +318,7 @@ def test_initial_state_of_larger_lattices(kw, rho):
     sim = K.Simulation(**kw)
     sim.init(19, rho)
     n, n0, p = sim.get_state()
-    N = kw["L"] ** kw["d"]
+    N = kw["N"] if "N" in kw else kw["L"] ** kw["d"]
     st = O.init(N, kw["replicas"], 19, rho)
     assert (n == O.pack_words(st.n)).all() and (n0 == n).all()
     assert (p == np.uint64(0xFFFFFFFFFFFFFFFF)).all()
