@@ -8,12 +8,24 @@ state of one context is 192 MiB (n, n0, p); the three together, 576 MiB,
 exceed the 126 MB L2, so no L2 flush is needed between steps.
 
 Metric: attempted KA moves per second counted per site x replica
-(N * R * sweeps / time), whole job.  Printed as one JSON line on rank 0.
+(N * R * sweeps / time), whole job.  Printed as one JSON line on rank 0,
+which also carries (one GPU):
+
+* ``roofline``: the dominant kernel (k_pencils, the group launches along y
+  and z: four of the six launches of a sweep) at 32 algorithmic bytes per
+  site-word-sweep, beside the whole group-kernel path;
+* ``rrg``: the random regular graph workload N=2^20, z=4, m=2, 64 replicas,
+  rho = 0.55 .. 0.90, with its own roofline at 48 bytes per site-word-sweep;
+* ``batched``: a bounded sample of the 512-instance mix run batched and with
+  per-job launches on the same GPU (``batched_over_plain``);
+* ``cpu_baseline``: the CPU oracle on one core and on every host core
+  (processes over replica blocks), with the core count and CPU model.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--sweeps S] [--impl native|reference]
 
 --impl reference times the CPU oracle (the serial restatement of the paper
-used by the tests) on a bounded sample of the same workload.
+used by the tests) on every host core, on a bounded sample of the same
+workload.
 
 Two more workloads, each printing its own JSON line (one GPU):
 
@@ -24,7 +36,9 @@ from __future__ import annotations
 
 import argparse
 import json
+import multiprocessing as mp
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -41,11 +55,20 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy peak is the 
 RHOS = (0.80, 0.85, 0.88)
 N_SITES = L ** D
 WORDS = R // 64
+GROUPS = 2 * D  # group launches per sweep and plane set: (mu, parity)
 BYTES_PER_SITE_WORD_SWEEP = 32  # read + write of n and p, 8 bytes each
 METRIC = "attempted KA moves/s (site x replica)"
 UNIT = "site-replica moves/s"
 WORKLOAD = ("cubic d=3 L=128 z=6 m=3, 256 replicas, rho in {0.80,0.85,0.88}, "
             "Philox seed 1, periodic")
+# random regular graphs: N=2^20, z=4, m=2, 64 replicas, rho 0.55 .. 0.90
+RRG_N, RRG_Z, RRG_M, RRG_R, RRG_GRAPH_SEED = 1 << 20, 4, 2, 64, 1
+RRG_RHOS = tuple(round(0.55 + 0.05 * k, 2) for k in range(8))
+RRG_BYTES_PER_SITE_WORD_SWEEP = 32 + 4 * RRG_Z  # + the int32 neighbour row of every site
+PROFILE_STREAM = os.path.join("profiles", "k_pencils_L128_R256.md")
+SRC_STREAM = os.path.join("paper_1710_05155_gb300", "csrc", "ka_cubic_stream.cuh")
+PROFILE_GRAPH = os.path.join("profiles", "k_graph_class_rrg_N2p20_R64.md")
+SRC_GRAPH = os.path.join("paper_1710_05155_gb300", "csrc", "ka_sweep_graph.cu")
 
 
 def _peaks():
@@ -112,20 +135,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def measured_traffic():
-    """DRAM bytes per k_cubic_group launch from the committed ncu summary, or
-    None when the kernel source changed since that capture."""
+def measured_traffic(profile: str, source: str):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    kernel source changed since that capture (its hash is in the summary)."""
     import hashlib
 
-    prof = os.path.join(ROOT, "profiles", "k_cubic_group_L128_R256.md")
-    src = os.path.join(ROOT, "paper_1710_05155_gb300", "csrc", "ka_cubic_kernel.cuh")
     try:
         fields = {}
-        for line in open(prof):
+        for line in open(os.path.join(ROOT, profile)):
             if ":" in line:
                 k, v = line.split(":", 1)
                 fields[k.strip()] = v.strip()
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        digest = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()[:16]
         if fields.get("kernel_source_sha256_16") != digest:
             return None
         return float(fields["traffic_bytes_per_launch"])
@@ -133,16 +154,100 @@ def measured_traffic():
         return None
 
 
-def oracle_sample(n_rep: int, sweeps: int, rho: float = RHOS[0]):
-    """Time the oracle on n_rep replicas of the workload (initial state untimed)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def _oracle_worker(conn, r0: int, n_rep: int, rho: float) -> None:
+    """One oracle process: replicas r0 .. r0 + n_rep - 1 of the cubic workload;
+    answers every "sweep k" message with the seconds its k sweeps took."""
     import oracle as O
 
     topo = O.cubic(D, L)
-    st = O.init(topo.N, n_rep, SEED, rho)
-    t0 = time.perf_counter()
-    O.sweeps(topo, M, st, SEED, sweeps)
-    dt = time.perf_counter() - t0
-    return N_SITES * n_rep * sweeps / dt, dt
+    st = O.init(topo.N, n_rep, SEED, rho, r0=r0)
+    conn.send("ready")
+    while True:
+        k = conn.recv()
+        if k is None:
+            break
+        t0 = time.perf_counter()
+        O.sweeps(topo, M, st, SEED, k)
+        conn.send(time.perf_counter() - t0)
+    conn.close()
+
+
+class OracleBlocks:
+    """The CPU oracle over `workers` processes (spawned), each holding its own
+    block of replicas of the cubic workload: replicas are independent, so the
+    blocks sweep in parallel.  step(k) runs k sweeps on every block and
+    returns the wall time until the last block is done."""
+
+    def __init__(self, workers: int, n_rep: int, rho: float = RHOS[0]):
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for w in range(workers):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, w * n_rep, n_rep, rho), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        for c in self.conns:
+            assert c.recv() == "ready"
+        self.workers, self.n_rep = workers, n_rep
+
+    def step(self, k: int) -> float:
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send(k)
+        for c in self.conns:
+            c.recv()
+        return time.perf_counter() - t0
+
+    def close(self) -> None:
+        for c in self.conns:
+            c.send(None)
+        for p in self.procs:
+            p.join(timeout=30)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(n_rep: int = 8, sweeps: int = 4) -> dict:
+    """The oracle on one core and on every host core (n_rep replicas per
+    process, `sweeps` sweeps after an untimed initial state)."""
+    cores = host_cores()
+    out = {"unit": UNIT, "kind": "oracle", "cpu_model": cpu_model(), "nproc": cores}
+    for key, workers in (("one_core", 1), ("all_cores", cores)):
+        blocks = OracleBlocks(workers, n_rep)
+        dt = blocks.step(sweeps)
+        blocks.close()
+        out[key] = {"value": N_SITES * n_rep * workers * sweeps / dt, "cores": workers,
+                    "seconds": dt,
+                    "sample": f"L=128 d=3 m=3 rho=0.80, {n_rep * workers} of 256 replicas "
+                              f"({n_rep} per process), {sweeps} sweeps"}
+    out["value"] = out["all_cores"]["value"]
+    out["cores"] = cores
+    out["sample"] = out["all_cores"]["sample"] + "; one core: " + out["one_core"]["sample"]
+    return out
 
 
 def workload_config(world: int, sweeps: int) -> dict:
@@ -152,63 +257,29 @@ def workload_config(world: int, sweeps: int) -> dict:
             "l2": "inputs larger than L2 (576 MiB of state per GPU)"}
 
 
-def native_line(*, world, steps, warmup, sweeps, ms, value, achieved, peak, peak_kind, traffic,
-                avg_launch_ms, isolated_launch_ms, bytes_per_launch, cpu, e2e_value, h2d, d2h,
-                gpu_launches, clocks) -> dict:
-    """The JSON line of the native cubic arm from its measured numbers."""
-    return {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
-        "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": workload_config(world, sweeps),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                     "kernel": "k_cubic_group", "peak_kind": peak_kind,
-                     "avg_launch_us": 1000.0 * avg_launch_ms,
-                     "avg_launch_us_isolated": 1000.0 * isolated_launch_ms,
-                     "bytes_per_launch": bytes_per_launch,
-                     # the DRAM bytes the kernel really moves per launch (the committed
-                     # ncu capture) over the same live launch time
-                     "dram_achieved": (traffic / (avg_launch_ms / 1000.0) / 1e9
-                                       if traffic else None),
-                     "dram_frac": (traffic / (avg_launch_ms / 1000.0) / 1e9 / peak
-                                   if traffic else None)},
-        "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
-        # a sweep attempts each of the N z / 2 bonds once per replica: z / 2 = d
-        # bond attempts per site-replica move
-        "bond_attempts_per_s": value * D,
-        "gpu_launches": gpu_launches,
-        "clocks": clocks,
-    }
-
-
 def run_reference(args, rank: int) -> None:
+    """The oracle on every host core, each step one sweep of a block of 4
+    replicas per process (rank 0 only; other ranks exit without work)."""
     if rank != 0:
         return
-    import oracle as O
-
-    topo = O.cubic(D, L)
+    cores = args.ref_cores or host_cores()
     n_rep = 4
-    st = O.init(topo.N, n_rep, SEED, RHOS[0])
+    blocks = OracleBlocks(cores, n_rep)
     for _ in range(args.warmup):
-        O.sweeps(topo, M, st, SEED, 1)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        O.sweeps(topo, M, st, SEED, 1)
-    dt = time.perf_counter() - t0
-    value = N_SITES * n_rep * args.steps / dt
-    sample = (f"oracle, 1 thread: L=128 d=3 m=3 rho=0.80, {n_rep} of 256 replicas, "
-              f"1 sweep per step")
+        blocks.step(1)
+    dt = sum(blocks.step(1) for _ in range(args.steps))
+    blocks.close()
+    value = N_SITES * n_rep * cores * args.steps / dt
+    sample = (f"oracle on {cores} processes ({cpu_model()}): L=128 d=3 m=3 rho=0.80, "
+              f"{n_rep * cores} of 256 replicas ({n_rep} per process), 1 sweep per step")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
         "config": workload_config(args.gpus, args.sweeps),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -229,6 +300,132 @@ def max_over_ranks(x: float, dist=None, device: str = "cpu") -> float:
 def rank_seed(rank: int) -> int:
     """Dynamics seed of a rank: every rank simulates its own replicas (weak scaling)."""
     return SEED + 1000 * rank
+
+
+def _apportion(region_ms: float, iso_ms: np.ndarray, dirs, launches: int) -> float:
+    """Average chained launch time (ms) of the launches of directions `dirs`:
+    the timed region split by the kernels' shares of the same launches timed
+    one by one (events around each)."""
+    share = float(iso_ms[list(dirs)].sum() / iso_ms.sum())
+    return region_ms * share / launches
+
+
+def run_rrg(dev: int, stream, sweeps: int) -> dict:
+    """Random regular graph N=2^20, z=4, m=2, 64 replicas: `sweeps` sweeps at
+    each of rho = 0.55 .. 0.90 (initial states untimed), CUDA events around
+    each density's sweeps; then one density's launches timed one by one."""
+    import torch
+
+    import paper_1710_05155_gb300 as K
+
+    t0 = time.perf_counter()
+    sim = K.Simulation(topo=K.KA_RRG, N=RRG_N, z=RRG_Z, m=RRG_M, replicas=RRG_R,
+                       graph_seed=RRG_GRAPH_SEED, device=dev, stream=stream)
+    build_s = time.perf_counter() - t0
+    nclass = sim.info["nclass"]
+    total_ms = 0.0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for rho in RRG_RHOS:
+        sim.init(SEED, rho)
+        K.ka_sweep(sim.ctx, 2)  # warm-up
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        K.ka_sweep(sim.ctx, sweeps)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        total_ms += ev0.elapsed_time(ev1)
+    moves = RRG_N * RRG_R * sweeps * len(RRG_RHOS)
+    value = moves / (total_ms / 1000.0)
+    K.ka_profile_enable(sim.ctx, True)
+    K.ka_sweep(sim.ctx, sweeps)
+    iso_ms, iso_n = K.ka_profile_read_dirs(sim.ctx)
+    K.ka_profile_enable(sim.ctx, False)
+    sim.close()
+    launches = nclass * sweeps * len(RRG_RHOS)
+    avg_ms = total_ms / launches  # the class launches are the whole timed region
+    sweep_ms = total_ms / (sweeps * len(RRG_RHOS))
+    bytes_per_sweep = RRG_BYTES_PER_SITE_WORD_SWEEP * RRG_N * (RRG_R // 64)
+    achieved = bytes_per_sweep / (sweep_ms / 1000.0) / 1e9
+    peak, peak_kind = _peaks()
+    traffic = measured_traffic(PROFILE_GRAPH, SRC_GRAPH)
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT,
+        "workload": f"RRG N=2^20 z=4 m=2, 64 replicas, rho {RRG_RHOS[0]}..{RRG_RHOS[-1]} "
+                    f"(8 densities), graph seed 1, Philox seed 1, {sweeps} sweeps each",
+        "ms_per_sweep": sweep_ms, "classes_per_sweep": nclass,
+        "graph_build_s": build_s,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_graph_class",
+                     "peak_kind": peak_kind,
+                     "bytes_per_site_word_sweep": RRG_BYTES_PER_SITE_WORD_SWEEP,
+                     "avg_launch_us": 1000.0 * avg_ms,
+                     "avg_launch_us_isolated": 1000.0 * float(iso_ms.sum() / max(iso_n.sum(), 1))},
+        "gpu_launches": launches,
+    }
+
+
+def run_batched_sample(dev: int, jobs_n: int, scale: float) -> dict:
+    """A bounded sample of the 512-instance mix, batched and per-job plain."""
+    import paper_1710_05155_gb300 as K
+    from paper_1710_05155_gb300 import workloads
+
+    jobs = workloads.instance_mix(512, master=1)[:jobs_n]
+    jobs = [workloads.Job(j.params, max(1, round(j.sweeps * scale)), j.every, j.seed, j.rho)
+            for j in jobs]
+    moves = float(sum(j.work for j in jobs))
+    t0 = time.perf_counter()
+    ms_b, rounds, k = _run_batch(jobs, K.KA_BATCH_GRAPH, dev, 0)
+    ms_p, _, _ = _run_batch(jobs, K.KA_BATCH_PLAIN, dev, k)
+    return {"value": moves / (ms_b / 1000.0), "unit": UNIT,
+            "workload": f"the first {jobs_n} of the 512-instance mix (cubic d=3 m=3 L in "
+                        f"{{16..96}} or RRG z=4 m=2 N=2^12..2^18, R=64), sweeps x {scale}",
+            "plain": moves / (ms_p / 1000.0), "ms": ms_b, "plain_ms": ms_p,
+            "batched_over_plain": ms_p / ms_b, "round_sweeps": k, "rounds": rounds,
+            "wall_s": time.perf_counter() - t0}
+
+
+def native_line(*, world, steps, warmup, sweeps, ms, value, achieved, peak, peak_kind, traffic,
+                pencil_ms, pencil_iso_ms, row_ms, row_iso_ms, bytes_per_launch, nq,
+                path_achieved, cpu, e2e_value, h2d, d2h, gpu_launches, clocks,
+                extra=None) -> dict:
+    """The JSON line of the native cubic arm from its measured numbers (times
+    in ms; rates in GB/s)."""
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": workload_config(world, sweeps),
+        "roofline": {
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+            "kernel": "k_pencils", "peak_kind": peak_kind,
+            "bytes_per_launch": bytes_per_launch, "planes_per_launch": nq,
+            "avg_launch_us": 1000.0 * pencil_ms,
+            "avg_launch_us_isolated": 1000.0 * pencil_iso_ms,
+            # the DRAM bytes the kernel moves per launch (the committed ncu
+            # capture) over the same launch time
+            "dram_achieved": traffic / (pencil_ms / 1000.0) / 1e9 if traffic else None,
+            "dram_frac": traffic / (pencil_ms / 1000.0) / 1e9 / peak if traffic else None,
+            "k_rows": {"avg_launch_us": 1000.0 * row_ms,
+                       "avg_launch_us_isolated": 1000.0 * row_iso_ms,
+                       "achieved": bytes_per_launch / (row_ms / 1000.0) / 1e9},
+            # every group launch and observation of the timed region together
+            "path_achieved": path_achieved, "path_frac": path_achieved / peak,
+        },
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        # a sweep attempts each of the N z / 2 bonds once per replica: z / 2 = d
+        # bond attempts per site-replica move
+        "bond_attempts_per_s": value * D,
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+    }
+    line.update(extra or {})
+    if "batched" in line:
+        line["batched_over_plain"] = line["batched"]["batched_over_plain"]
+    return line
 
 
 def run_native(args, rank: int, world: int) -> None:
@@ -253,10 +450,11 @@ def run_native(args, rank: int, world: int) -> None:
         sim.init(rank_seed(rank), rho)
         sims.append(sim)
     counts_dev = [torch.zeros((R, 4), dtype=torch.int64, device=f"cuda:{dev}") for _ in sims]
-    P = sims[0].info["planes"]
-    V = sims[0].info["plane_words"]
-    groups = 2 * D
-    launches_per_step = len(sims) * (P * S * groups + 1)
+    info = sims[0].info
+    P, nq = info["planes"], info["planes_per_launch"]
+    sets = -(-P // nq)  # launches per group and sweep
+    sweep_launches_per_step = len(sims) * sets * S * GROUPS
+    launches_per_step = sweep_launches_per_step + len(sims)  # + one observation each
 
     def step():
         for sim, cd in zip(sims, counts_dev):
@@ -287,23 +485,31 @@ def run_native(args, rank: int, world: int) -> None:
     moves = N_SITES * R * S * len(sims) * args.steps * world
     value = moves / (ms / 1000.0)
 
-    # The pencil kernel's launch duration over the timed region: its launches
-    # are 99.8 % of the step's device time (the rest is one observation per
-    # context and step), so the region's event time over its sweep launches is
-    # a slightly conservative average launch, taken as the launches ran there
-    # (chained).  Beside it, the same kernel timed launch by launch with
-    # events around each (isolated: no overlap between launches).
-    sweep_launches = len(sims) * P * S * groups * args.steps
-    avg_launch_ms = local_ms / sweep_launches
-    bytes_per_launch = BYTES_PER_SITE_WORD_SWEEP * N_SITES * V / groups
-    achieved = bytes_per_launch / (avg_launch_ms / 1000.0) / 1e9
-    K.ka_profile_enable(sims[0].ctx, True)
-    K.ka_sweep(sims[0].ctx, S)
-    kms, nl = K.ka_profile_read(sims[0].ctx)
-    K.ka_profile_enable(sims[0].ctx, False)
-    isolated_launch_ms = kms / max(nl, 1)
+    # Roofline.  The group launches are the timed region (one observation per
+    # context and step aside).  The same launches of one step, timed one by
+    # one with events around each (ka_profile_read_dirs, by direction), give
+    # each kernel's share of the region: k_rows runs the groups along x,
+    # k_pencils those along y and z (two thirds of the launches).  A launch
+    # covers nq planes of one group: 32 bytes per site-word-sweep / 6 groups.
+    iso_ms, iso_n = np.zeros(4), np.zeros(4, np.int64)
+    for sim in sims:
+        K.ka_profile_enable(sim.ctx, True)
+        K.ka_sweep(sim.ctx, S)
+        a_ms, a_n = K.ka_profile_read_dirs(sim.ctx)
+        K.ka_profile_enable(sim.ctx, False)
+        iso_ms += a_ms
+        iso_n += a_n
+    region_launches = sweep_launches_per_step * args.steps
+    pencil_launches = region_launches * 2 // 3
+    row_launches = region_launches - pencil_launches
+    bytes_per_launch = BYTES_PER_SITE_WORD_SWEEP * N_SITES * nq / GROUPS
+    pencil_ms = _apportion(local_ms, iso_ms, (1, 2), pencil_launches)
+    row_ms = _apportion(local_ms, iso_ms, (0,), row_launches)
+    achieved = bytes_per_launch / (pencil_ms / 1000.0) / 1e9
+    path_achieved = BYTES_PER_SITE_WORD_SWEEP * N_SITES * WORDS * S * len(sims) * args.steps / (
+        local_ms / 1000.0) / 1e9
     peak, peak_kind = _peaks()
-    traffic = measured_traffic()
+    traffic = measured_traffic(PROFILE_STREAM, SRC_STREAM)
 
     # end to end through the C ABI: initial state from pinned host memory,
     # S sweeps, counts back to the host, for every context.  Each context runs
@@ -352,25 +558,27 @@ def run_native(args, rank: int, world: int) -> None:
     e2e_value = N_SITES * R * S * len(sims) * e2e_steps * world / e2e_s
     h2d = len(sims) * 3 * WORDS * N_SITES * 8
     d2h = len(sims) * R * 4 * 8
-
-    if rank == 0:
-        cpu = None
-        if world == 1 and not args.no_cpu_baseline:
-            n_rep, sw = 8, 2
-            v, dt = oracle_sample(n_rep, sw)
-            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"L=128 d=3 m=3 rho=0.80, {n_rep} of 256 replicas, {sw} sweeps "
-                             f"after an untimed init ({dt:.1f} s)"}
-        line = native_line(world=world, steps=args.steps, warmup=args.warmup, sweeps=S, ms=ms,
-                           value=value, achieved=achieved, peak=peak, peak_kind=peak_kind,
-                           traffic=traffic, avg_launch_ms=avg_launch_ms,
-                           isolated_launch_ms=isolated_launch_ms,
-                           bytes_per_launch=bytes_per_launch, cpu=cpu, e2e_value=e2e_value,
-                           h2d=h2d, d2h=d2h, gpu_launches=launches_per_step * args.steps,
-                           clocks=clk)
-        print(json.dumps(line), flush=True)
     for sim in sims + e2e_sims:
         sim.close()
+
+    if rank == 0:
+        extra = {}
+        if world == 1:
+            if not args.no_rrg:
+                extra["rrg"] = run_rrg(dev, stream, args.rrg_sweeps)
+            if not args.no_batched:
+                extra["batched"] = run_batched_sample(dev, args.batched_jobs, args.batched_scale)
+            if not args.no_cpu_baseline:
+                extra["cpu_baseline"] = cpu_baseline()
+        line = native_line(
+            world=world, steps=args.steps, warmup=args.warmup, sweeps=S, ms=ms, value=value,
+            achieved=achieved, peak=peak, peak_kind=peak_kind, traffic=traffic,
+            pencil_ms=pencil_ms, pencil_iso_ms=float(iso_ms[1:3].sum() / iso_n[1:3].sum()),
+            row_ms=row_ms, row_iso_ms=float(iso_ms[0] / iso_n[0]),
+            bytes_per_launch=bytes_per_launch, nq=nq, path_achieved=path_achieved,
+            cpu=extra.pop("cpu_baseline", None), e2e_value=e2e_value, h2d=h2d, d2h=d2h,
+            gpu_launches=launches_per_step * args.steps, clocks=clk, extra=extra)
+        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
@@ -483,6 +691,15 @@ def main():
     ap.add_argument("--sweeps", type=int, default=100, help="sweeps per context per step")
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-cores", type=int, default=0,
+                    help="reference arm: oracle processes (0: every host core)")
+    ap.add_argument("--no-rrg", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--rrg-sweeps", type=int, default=100, help="rrg: sweeps per density")
+    ap.add_argument("--batched-jobs", type=int, default=128,
+                    help="batched sample of the main line: instances of the mix")
+    ap.add_argument("--batched-scale", type=float, default=0.05,
+                    help="batched sample of the main line: fraction of each job's sweeps")
     ap.add_argument("--workload", choices=["cubic", "batched", "served"], default="cubic")
     ap.add_argument("--jobs", type=int, default=0, help="instances (batched: 512, served: 100)")
     ap.add_argument("--sweep-scale", type=float, default=0.05,

@@ -127,8 +127,11 @@ typedef struct {
     int32_t kernel;     /* 0 = cubic pencil kernel, 1 = edge-gather kernel */
     int32_t rrg_attempts; /* configuration-model attempts (KA_RRG) */
     size_t device_bytes;  /* device memory the context uses */
-    int32_t planes;       /* device state planes per array (sweep launches per class group) */
+    int32_t planes;       /* device state planes per array */
     int32_t plane_words;  /* words per site in one plane */
+    int32_t planes_per_launch; /* planes one sweep launch covers (cubic group
+                                  launches per class group and sweep:
+                                  ceil(planes / planes_per_launch)) */
 } ka_info_t;
 
 /* Device bytes ka_create_in needs for these parameters. */
@@ -251,11 +254,18 @@ ka_status ka_build_topology(const ka_params *params, int64_t *nclass, int64_t *n
 ka_status ka_layered_graph(int32_t d, int32_t L, int32_t M, uint64_t graph_seed, int32_t *nbr);
 
 /* Kernel timing for roofline reports.  When enabled, ka_sweep brackets
- * every sweep-kernel launch with CUDA events on the context stream;
- * ka_profile_read synchronises and returns the summed kernel time and the
- * number of launches since the last read. */
+ * every sweep-kernel launch with CUDA events on the context stream (the
+ * events sit between launches that would otherwise overlap their prologues,
+ * so the times are those of launches run one after the other).
+ * ka_profile_read synchronises and returns the summed kernel time (ms) and
+ * the number of launches since the last read; ka_profile_read_dirs returns
+ * the same split by bond direction: host arrays kernel_ms[4] and
+ * launches[4], entry mu for the group launches of direction mu on cubic
+ * lattices, entry 0 for every class launch on graphs.  Either read clears
+ * all sums.  KA_EINVAL for a NULL context; KA_ECUDA if an event fails. */
 ka_status ka_profile_enable(ka_ctx *ctx, int32_t enable);
 ka_status ka_profile_read(ka_ctx *ctx, double *kernel_ms, int64_t *launches);
+ka_status ka_profile_read_dirs(ka_ctx *ctx, double *kernel_ms, int64_t *launches);
 
 /* Destroy a context (NULL is fine).  Synchronises; returns a deferred
  * kernel error if one is pending. */
@@ -338,6 +348,13 @@ ka_status ka_batch_poll(const ka_batch *b, int64_t job_id, int64_t *sweep, int32
  * [n_obs][R][4] (as ka_observe). */
 ka_status ka_batch_observations(const ka_batch *b, int64_t job_id, int64_t *n_obs,
                                 int64_t *obs_sweeps, int64_t *counts);
+
+/* State of a job (its current sweep: ka_batch_poll) copied to host arrays in
+ * the canonical layout of ka_get_state, [R/64][N] uint64 each; any pointer
+ * may be NULL.  Synchronises the batch stream.  KA_EINVAL for an unknown
+ * job; the status of ka_get_state otherwise (a deferred device error of the
+ * job's launches included). */
+ka_status ka_batch_state(ka_batch *b, int64_t job_id, uint64_t *n, uint64_t *n0, uint64_t *p);
 
 /* Retire a job and free its memory (finished or not). */
 ka_status ka_batch_remove(ka_batch *b, int64_t job_id);

@@ -49,7 +49,8 @@ class ka_info_t(C.Structure):
                 ("words", C.c_int32), ("nclass", C.c_int64), ("nbonds", C.c_int64),
                 ("sweep", C.c_int64), ("K", C.c_int64), ("seed", C.c_uint64),
                 ("kernel", C.c_int32), ("rrg_attempts", C.c_int32), ("device_bytes", C.c_size_t),
-                ("planes", C.c_int32), ("plane_words", C.c_int32)]
+                ("planes", C.c_int32), ("plane_words", C.c_int32),
+                ("planes_per_launch", C.c_int32)]
 
 
 _lib = None
@@ -77,6 +78,7 @@ _SIGS = {
                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ka_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "ka_profile_read": (C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_int64)]),
+    "ka_profile_read_dirs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "ka_observe_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                     C.c_void_p, C.c_void_p]),
     "ka_batch_create": (C.c_int, [C.c_int32, C.c_void_p, C.c_size_t, C.c_int32, _P(C.c_void_p)]),
@@ -89,6 +91,7 @@ _SIGS = {
     "ka_batch_step": (C.c_int, [C.c_void_p, C.c_int64, _P(C.c_int64)]),
     "ka_batch_autotune": (C.c_int, [C.c_void_p, _P(C.c_int64)]),
     "ka_batch_poll": (C.c_int, [C.c_void_p, C.c_int64, _P(C.c_int64), _P(C.c_int32)]),
+    "ka_batch_state": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ka_batch_observations": (C.c_int, [C.c_void_p, C.c_int64, _P(C.c_int64), C.c_void_p,
                                         C.c_void_p]),
     "ka_batch_remove": (C.c_int, [C.c_void_p, C.c_int64]),
@@ -333,6 +336,13 @@ def ka_profile_read(ctx: Ctx):
     return ms.value, n.value
 
 
+def ka_profile_read_dirs(ctx: Ctx):
+    """Summed kernel ms [4] and launches [4] by bond direction since the last read."""
+    ms, n = np.zeros(4, np.float64), np.zeros(4, np.int64)
+    _check(load().ka_profile_read_dirs(ctx.handle, _ptr(ms), _ptr(n)), "ka_profile_read_dirs", ctx)
+    return ms, n
+
+
 def ka_observe_static(n_ptr: int, n0_ptr: int, p_ptr: int, N: int, replicas: int,
                       stream: int | None = None) -> np.ndarray:
     """Counts [R, 4] of caller-held device state (canonical [R/64, N] layout),
@@ -412,6 +422,12 @@ class Batch:
         _check(load().ka_batch_observations(self.handle, job, C.byref(n), _ptr(sw), _ptr(cnt)),
                "ka_batch_observations")
         return sw, cnt
+
+    def state(self, job: int, words: int, N: int):
+        """(n, n0, p) of a job, each [R/64, N] uint64 in canonical layout."""
+        out = [np.zeros((words, N), np.uint64) for _ in range(3)]
+        _check(load().ka_batch_state(self.handle, job, *(_ptr(a) for a in out)), "ka_batch_state")
+        return tuple(out)
 
     def remove(self, job: int) -> None:
         _check(load().ka_batch_remove(self.handle, job), "ka_batch_remove")

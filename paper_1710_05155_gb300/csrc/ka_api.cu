@@ -236,7 +236,19 @@ cudaEvent_t next_event(ka_ctx* c) {
   return c->ev[c->ev_used++];
 }
 
-// accumulate the elapsed time of recorded event pairs
+// Start timing one sweep-kernel launch of direction dir when profiling is
+// on: records the first event of a pair and returns the second (nullptr when
+// off), which the caller records after the launch.
+cudaEvent_t prof_begin(ka_ctx* c, int dir) {
+  if (!c->prof) return nullptr;
+  cudaEvent_t e0 = next_event(c), e1 = next_event(c);
+  if (!e0 || !e1) return nullptr;
+  c->ev_dir.push_back(dir);
+  cudaEventRecord(e0, c->stream);
+  return e1;
+}
+
+// accumulate the elapsed time of recorded event pairs by direction
 ka_status drain_profile(ka_ctx* c) {
   if (c->ev_used == 0) return KA_OK;
   cudaError_t e = cudaEventSynchronize(c->ev[c->ev_used - 1]);
@@ -245,10 +257,12 @@ ka_status drain_profile(ka_ctx* c) {
     float ms = 0.f;
     e = cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]);
     if (e) return cuda_fail(c, e, "profile elapsed");
-    c->prof_ms += ms;
-    c->prof_launches++;
+    const int dir = c->ev_dir[k / 2];
+    c->prof_ms[dir] += ms;
+    c->prof_launches[dir]++;
   }
   c->ev_used = 0;
+  c->ev_dir.clear();
   return KA_OK;
 }
 
@@ -365,12 +379,7 @@ ka_status ka_sweep(ka_ctx* c, int64_t n) {
       for (int64_t s = 0; s < n && !e; ++s)
         for (int mu = 0; mu < 3 && !e; ++mu)
           for (int par = 0; par < 2 && !e; ++par) {
-            cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (c->prof) {
-              e0 = next_event(c);
-              e1 = next_event(c);
-              if (e0) cudaEventRecord(e0, c->stream);
-            }
+            cudaEvent_t e1 = prof_begin(c, mu);
             e = ka::launch_stream_group(c->pl, q0, cnt, c->L, c->m, mu, par,
                                         (uint32_t)(c->sweep + s), c->rk, c->stream);
             if (e1) cudaEventRecord(e1, c->stream);
@@ -384,12 +393,7 @@ ka_status ka_sweep(ka_ctx* c, int64_t n) {
       for (int64_t s = 0; s < n && !e; ++s)
         for (int mu = 0; mu < c->d && !e; ++mu)
           for (int par = 0; par < npar && !e; ++par) {
-            cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (c->prof) {
-              e0 = next_event(c);
-              e1 = next_event(c);
-              if (e0) cudaEventRecord(e0, c->stream);
-            }
+            cudaEvent_t e1 = prof_begin(c, mu);
             e = ka::launch_cubic_group(c->pl, q, sh, mu, par, (uint32_t)(c->sweep + s), c->rk,
                                        c->stream);
             if (e1) cudaEventRecord(e1, c->stream);
@@ -397,12 +401,7 @@ ka_status ka_sweep(ka_ctx* c, int64_t n) {
   } else {
     for (int64_t s = 0; s < n && !e; ++s)
       for (int64_t cl = 0; cl < c->nclass && !e; ++cl) {
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (c->prof) {
-          e0 = next_event(c);
-          e1 = next_event(c);
-          if (e0) cudaEventRecord(e0, c->stream);
-        }
+        cudaEvent_t e1 = prof_begin(c, 0);
         const int64_t off = c->host.class_off[cl];
         e = ka::launch_graph_class(c->pl, c->g, off, c->host.class_off[cl + 1] - off,
                                    (uint32_t)cl, (uint32_t)(c->sweep + s), c->rk, c->stream);
@@ -537,6 +536,8 @@ ka_status ka_info(const ka_ctx* c, ka_info_t* out) {
   out->device_bytes = c->bytes;
   out->planes = c->pl.P;
   out->plane_words = c->pl.V;
+  out->planes_per_launch =
+      (c->pencil && ka::stream_supported(c->d, c->L)) ? ka::stream_planes_per_launch(c->L, c->pl.P) : 1;
   return KA_OK;
 }
 
@@ -595,10 +596,30 @@ ka_status ka_profile_read(ka_ctx* c, double* kernel_ms, int64_t* launches) {
   DeviceGuard dg(c->device);
   ka_status s = drain_profile(c);
   if (s) return s;
-  if (kernel_ms) *kernel_ms = c->prof_ms;
-  if (launches) *launches = c->prof_launches;
-  c->prof_ms = 0.0;
-  c->prof_launches = 0;
+  double ms = 0.0;
+  int64_t nl = 0;
+  for (int k = 0; k < 4; ++k) {
+    ms += c->prof_ms[k];
+    nl += c->prof_launches[k];
+    c->prof_ms[k] = 0.0;
+    c->prof_launches[k] = 0;
+  }
+  if (kernel_ms) *kernel_ms = ms;
+  if (launches) *launches = nl;
+  return KA_OK;
+}
+
+ka_status ka_profile_read_dirs(ka_ctx* c, double* kernel_ms, int64_t* launches) {
+  if (!c) return KA_EINVAL;
+  DeviceGuard dg(c->device);
+  ka_status s = drain_profile(c);
+  if (s) return s;
+  for (int k = 0; k < 4; ++k) {
+    if (kernel_ms) kernel_ms[k] = c->prof_ms[k];
+    if (launches) launches[k] = c->prof_launches[k];
+    c->prof_ms[k] = 0.0;
+    c->prof_launches[k] = 0;
+  }
   return KA_OK;
 }
 

@@ -628,6 +628,15 @@ ka_status ka_batch_observations(const ka_batch* b, int64_t job_id, int64_t* n_ob
   return KA_OK;
 }
 
+ka_status ka_batch_state(ka_batch* b, int64_t job_id, uint64_t* n, uint64_t* n0, uint64_t* p) {
+  if (!b) return KA_EINVAL;
+  auto it = b->jobs.find(job_id);
+  if (it == b->jobs.end()) return KA_EINVAL;
+  DeviceScope scope(b->device);
+  // the job's context runs on the batch stream: ka_get_state waits for it
+  return ka_get_state(it->second->ctx, n, n0, p);
+}
+
 ka_status ka_batch_remove(ka_batch* b, int64_t job_id) {
   if (!b) return KA_EINVAL;
   auto it = b->jobs.find(job_id);

@@ -31,9 +31,10 @@ struct ka_ctx {
   // kernel timing
   bool prof = false;
   std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_dir;  // direction of every recorded event pair
   size_t ev_used = 0;
-  double prof_ms = 0.0;
-  int64_t prof_launches = 0;
+  double prof_ms[4] = {0.0, 0.0, 0.0, 0.0};  // by direction mu (graph classes: 0)
+  int64_t prof_launches[4] = {0, 0, 0, 0};
 };
 
 namespace ka {

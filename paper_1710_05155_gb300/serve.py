@@ -46,6 +46,7 @@ class Record:
     error: str = ""
     sweeps: np.ndarray | None = None
     counts: np.ndarray | None = None
+    state: tuple | None = None  # (n, n0, p) at the end, when the backend reports it
 
 
 def job_bytes(job, device: int = 0) -> int:
@@ -117,6 +118,10 @@ class DeviceBackend:
 
     def observations(self, job_id: int, replicas: int):
         return self.batch.observations(job_id, replicas)
+
+    def state(self, job_id: int, job):
+        """Final (n, n0, p) of a job, canonical [R/64, N] uint64 each."""
+        return self.batch.state(job_id, job.params["replicas"] // 64, job.sites)
 
     def remove(self, job_id: int) -> None:
         self.batch.remove(job_id)
@@ -212,6 +217,8 @@ class Server:
                         r.finished, r.status = now(), "done"
                         if self.keep_results:
                             r.sweeps, r.counts = be.observations(jid, r.job.params["replicas"])
+                            if hasattr(be, "state"):
+                                r.state = be.state(jid, r.job)
                         be.remove(jid)
                 elif preparing:
                     cf.wait(list(preparing), timeout=0.01, return_when=cf.FIRST_COMPLETED)

@@ -1,11 +1,11 @@
-"""Batched execution: every job gives the same result alone and in the mix.
+"""Batched execution: every job in the mix gives the oracle's result.
 
 A batch advances many jobs of uneven size and type together (one launch per
 bond-class group for all cubic jobs of a shape class, one per colour class for
 all graph jobs); the random streams are keyed by each job's own seed, sweep,
-class and site, so each job's observations must equal, bit for bit, those of
-the same job run alone through a plain context -- which the parity tests tie
-to the oracle.  Also: admission by memory budget, removal, autotuning.
+class and site, so each job's observations and final state planes must equal,
+bit for bit, those of the oracle running that job alone.  Also: admission by
+memory budget, removal, autotuning, adoption of a running context.
 """
 import numpy as np
 import pytest
@@ -16,6 +16,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover - CPU-only hosts
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
+import oracle_runs  # noqa: E402
 import paper_1710_05155_gb300 as K  # noqa: E402
 
 JOBS = [
@@ -54,9 +55,30 @@ def _alone(job):
     return np.array(sweeps), np.stack(counts)
 
 
+@pytest.fixture(scope="module")
+def oracle_results():
+    """The oracle's run of every job of JOBS: sweeps, counts, n, n0, p."""
+    return oracle_runs.run_jobs([(j["params"], j["sweeps"], j["every"], j["seed"], j["rho"])
+                                 for j in JOBS])
+
+
+def _sites(params):
+    return params["L"] ** params["d"] if params["topo"] == K.KA_CUBIC else params["N"]
+
+
+def _check_job(b, jid, job, want):
+    sw, cnt = b.observations(jid, job["params"]["replicas"])
+    w_sw, w_cnt, w_n, w_n0, w_p = want
+    assert (sw == w_sw).all(), f"job {jid}: observation sweeps differ"
+    assert (cnt == w_cnt).all(), f"job {jid}: counts differ from the oracle's"
+    n, n0, p = b.state(jid, job["params"]["replicas"] // 64, _sites(job["params"]))
+    assert (n == w_n).all() and (n0 == w_n0).all() and (p == w_p).all(), \
+        f"job {jid}: final state differs from the oracle's"
+
+
 @pytest.mark.parametrize("flags,k", [(K.KA_BATCH_GRAPH, 8), (0, 5), (K.KA_BATCH_PLAIN, 6),
                                      (K.KA_BATCH_GRAPH, 1)])
-def test_jobs_alone_equal_jobs_in_the_mix(flags, k):
+def test_batched_jobs_match_the_oracle(flags, k, oracle_results):
     with K.Batch(flags=flags) as b:
         ids = [b.add(j["sweeps"], j["every"], j["seed"], j["rho"], **j["params"]) for j in JOBS]
         for _ in range(1000):
@@ -64,18 +86,15 @@ def test_jobs_alone_equal_jobs_in_the_mix(flags, k):
                 break
             b.step(k)
         assert b.info()["active"] == 0
-        for jid, job in zip(ids, JOBS):
+        for jid, job, want in zip(ids, JOBS, oracle_results):
             t, done = b.poll(jid)
             assert done and t == job["sweeps"]
-            sw, cnt = b.observations(jid, job["params"]["replicas"])
-            want_sw, want_cnt = _alone(job)
-            assert (sw == want_sw).all()
-            assert (cnt == want_cnt).all(), f"job {jid} differs from its solo run"
+            _check_job(b, jid, job, want)
 
 
-def test_jobs_joining_a_running_batch():
+def test_jobs_joining_a_running_batch(oracle_results):
     # continuous batching: a job admitted while others are mid-run still
-    # matches its solo run
+    # gives the oracle's result
     with K.Batch() as b:
         first = [b.add(j["sweeps"], j["every"], j["seed"], j["rho"], **j["params"]) for j in JOBS[:4]]
         b.step(6)
@@ -83,10 +102,22 @@ def test_jobs_joining_a_running_batch():
         late = [b.add(j["sweeps"], j["every"], j["seed"], j["rho"], **j["params"]) for j in JOBS[4:]]
         while b.info()["active"]:
             b.step(4)
-        for jid, job in zip(first + late, JOBS):
-            sw, cnt = b.observations(jid, job["params"]["replicas"])
-            want_sw, want_cnt = _alone(job)
-            assert (sw == want_sw).all() and (cnt == want_cnt).all()
+        for jid, job, want in zip(first + late, JOBS, oracle_results):
+            _check_job(b, jid, job, want)
+
+
+def test_solo_runs_match_the_oracle(oracle_results):
+    # the plain (single-context) path of the same jobs, observation by observation
+    for job, want in zip(JOBS, oracle_results):
+        sw, cnt = _alone(job)
+        assert (sw == want[0]).all() and (cnt == want[1]).all()
+
+
+def test_job_state_of_an_unknown_job_is_rejected():
+    with K.Batch() as b:
+        with pytest.raises(K.KaError) as e:
+            b.state(12345, 1, 64)
+        assert e.value.status == K.KA_EINVAL
 
 
 def test_budget_admission_and_release():

@@ -268,6 +268,45 @@ def test_large_rrg_prefix():
     _assert_same(sim, st, "after 2 sweeps")
 
 
+def _rrg_bits(N, z, m, graph_seed, R0, Rs, seed, rho, sweeps):
+    """Replicas R0 .. R0 + Rs - 1 of a random regular graph run by the oracle
+    (in a worker process): n, p as [N, Rs] bytes, and their counts."""
+    topo = O.rrg(N, z, graph_seed)
+    st = O.init(N, Rs, seed, rho, r0=R0)
+    O.sweeps(topo, m, st, seed, sweeps)
+    return st.n, st.p, O.observe(st)
+
+
+def test_large_rrg_twenty_sweeps_sampled_replicas():
+    """Random regular graph N=2^20, z=4, m=2, 64 replicas at rho = 0.55 and
+    0.90 (the ends of the density range), 20 sweeps in one call: replicas
+    0-7 and 56-63 bit for bit against the oracle run on those replicas
+    alone, with their counts."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    N, z, m, R, seed, sweeps, nb = 1 << 20, 4, 2, 64, 1, 20, 8
+    samples = (0, 56)
+    rhos = (0.55, 0.90)
+    with cf.ProcessPoolExecutor(max_workers=4, mp_context=mp.get_context("spawn")) as pool:
+        futs = {(rho, b): pool.submit(_rrg_bits, N, z, m, 1, b, nb, seed, rho, sweeps)
+                for rho in rhos for b in samples}
+        for rho in rhos:
+            sim = K.Simulation(topo=K.KA_RRG, N=N, z=z, m=m, replicas=R, graph_seed=1)
+            sim.init(seed, rho)
+            sim.sweep(sweeps)
+            n, _, p = sim.get_state()
+            _, counts = sim.observe()
+            sim.close()
+            for b in samples:
+                on, op, oc = futs[(rho, b)].result()
+                shifts = np.arange(b, b + nb, dtype=np.uint64)
+                bits = lambda w: ((w[0][:, None] >> shifts) & np.uint64(1)).astype(np.uint8)
+                assert (bits(n) == on).all(), f"n rho={rho} replicas {b}..{b + nb - 1}"
+                assert (bits(p) == op).all(), f"p rho={rho} replicas {b}..{b + nb - 1}"
+                assert (counts[b:b + nb] == oc).all()
+
+
 def test_large_cubic_two_planes_sampled_words():
     """d=3, L=128, 512 replicas (eight one-word planes, four launches of two
     planes per group): words 3 and 7 against the oracle on their 64 replicas,

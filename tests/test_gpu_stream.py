@@ -118,3 +118,29 @@ def test_l128_bench_configuration_prefix():
                 assert (_bits(n[w], b, nb) == on).all(), f"n rho={rho} word {w}"
                 assert (_bits(p[w], b, nb) == op).all(), f"p rho={rho} word {w}"
                 assert (counts[64 * w + b:64 * w + b + nb] == oc).all()
+
+
+def test_profile_by_direction():
+    # one sweep of one plane set: two group launches per direction; a graph
+    # context books every class launch under direction 0
+    sim = K.Simulation(topo=K.KA_CUBIC, d=3, L=32, m=3, replicas=128)
+    assert sim.info["planes_per_launch"] == 2
+    sim.init(1, 0.8)
+    K.ka_profile_enable(sim.ctx, True)
+    sim.sweep(1)
+    ms, n = K.ka_profile_read_dirs(sim.ctx)
+    assert list(n) == [2, 2, 2, 0] and (ms[:3] > 0).all() and ms[3] == 0
+    sim.sweep(2)
+    tot, nl = K.ka_profile_read(sim.ctx)
+    assert nl == 12 and tot > 0
+    K.ka_profile_enable(sim.ctx, False)
+    sim.sweep(1)
+    assert K.ka_profile_read(sim.ctx)[1] == 0
+    sim.close()
+    g = K.Simulation(topo=K.KA_RRG, N=4096, z=4, m=2, replicas=64, graph_seed=3)
+    g.init(1, 0.7)
+    K.ka_profile_enable(g.ctx, True)
+    g.sweep(1)
+    ms, n = K.ka_profile_read_dirs(g.ctx)
+    assert n[0] == g.info["nclass"] and (n[1:] == 0).all()
+    g.close()
