@@ -10,7 +10,9 @@
 //
 // A plane holds V = 1, 2 or 4 words per site, so a site's words share one
 // 32-byte sector: every gather is a random access, and the sector is the
-// unit the memory system moves.  The partner's word is not gathered twice.
+// unit the memory system moves.  The partner's word is not gathered twice,
+// and p is never read: the bits of p that a swap clears are cleared by an
+// atomic AND in the L2.
 // A thread first loads what depends only on static tables (its bond, the
 // two neighbour rows) and computes the gate words, then gathers the state.
 // Single-instance class launches are chained with programmatic dependent
@@ -165,16 +167,18 @@ __device__ __forceinline__ void exchange(uint64_t* np, uint64_t* pp, int z, int3
   if (any) {
     st<V>(np, u, nu);
     st<V>(np, v, nv);
-    uint64_t pu[V], pv[V];
-    ld<V>(pp, u, pu);
-    ld<V>(pp, v, pv);
+    // Persistence: an atomic AND performed in the L2 (no reply), not a load
+    // of p after the swap is known and a store: random gathers are bound by
+    // the misses an SM keeps in flight, and this removes two of them per bond
+    // and a dependent round trip.
+    unsigned long long* pw = reinterpret_cast<unsigned long long*>(pp);
 #pragma unroll
     for (int h = 0; h < V; ++h) {
-      pu[h] &= ~sw[h];
-      pv[h] &= ~sw[h];
+      if (sw[h]) {
+        atomicAnd(pw + (size_t)V * u + h, (unsigned long long)~sw[h]);
+        atomicAnd(pw + (size_t)V * v + h, (unsigned long long)~sw[h]);
+      }
     }
-    st<V>(pp, u, pu);
-    st<V>(pp, v, pv);
   }
 }
 
