@@ -21,7 +21,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t n, n0, p, stage, counts, hist, pre_key, pre_idx, krem, unresolved, err, nbr, bu, bv, bid,
-      total;
+      perm, inv, total;
 };
 
 struct Shape {
@@ -95,7 +95,8 @@ Layout layout_of(const Shape& s) {
   l.n = take(plane);
   l.n0 = take(plane);
   l.p = take(plane);
-  l.stage = (s.V > 1 || s.xs) ? take(plane) : 0;  // layout conversion of get/set_state
+  // layout conversion of get/set_state (graphs: breadth-first storage order)
+  l.stage = (s.V > 1 || s.xs || s.topo != KA_CUBIC) ? take(plane) : 0;
   l.counts = take((size_t)s.R * 4 * sizeof(unsigned long long));
   l.hist = take((size_t)s.R * 256 * sizeof(uint32_t));
   l.pre_key = take((size_t)s.R * sizeof(uint64_t));
@@ -108,6 +109,10 @@ Layout layout_of(const Shape& s) {
     l.bu = take((size_t)s.E * sizeof(int32_t));
     l.bv = take((size_t)s.E * sizeof(int32_t));
     l.bid = take((size_t)s.E * sizeof(uint32_t));
+  }
+  if (s.topo != KA_CUBIC) {
+    l.perm = take((size_t)s.N * sizeof(int32_t));
+    l.inv = take((size_t)s.N * sizeof(int32_t));
   }
   l.total = off;
   return l;
@@ -164,7 +169,7 @@ ka_status create_common(const ka_params* params, void* buf, size_t bytes, bool o
   c->pl.xs = s.xs;
   c->err_dev = (int*)(base + l.err);
   c->counts_dev = (unsigned long long*)(base + l.counts);
-  c->stage = (s.V > 1 || s.xs) ? (uint64_t*)(base + l.stage) : nullptr;
+  c->stage = (s.V > 1 || s.xs || s.topo != KA_CUBIC) ? (uint64_t*)(base + l.stage) : nullptr;
   c->is.hist = (uint32_t*)(base + l.hist);
   c->is.pre_key = (uint64_t*)(base + l.pre_key);
   c->is.pre_idx = (uint32_t*)(base + l.pre_idx);
@@ -206,16 +211,38 @@ ka_status create_common(const ka_params* params, void* buf, size_t bytes, bool o
     c->g.z = s.z;
     c->g.m = s.m;
     c->g.cubic_L = (s.topo == KA_CUBIC) ? s.L : 0;
-    std::vector<uint32_t> bid32(c->host.bid.begin(), c->host.bid.end());
-    cudaError_t e = cudaMemcpyAsync((void*)c->g.nbr, c->host.nbr.data(),
-                                    c->host.nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
-                                    c->stream);
-    if (!e) e = cudaMemcpyAsync((void*)c->g.bu, c->host.bu.data(), c->host.bu.size() * 4,
+    // Device tables.  Graphs keep their sites in breadth-first order: the
+    // neighbour rows, the bonds (sorted by position inside each class) and
+    // the planes use storage positions; bond ids, classes and the state
+    // layout of the ABI stay canonical.  Cubic lattices on this path keep
+    // index order.
+    std::vector<int32_t> perm, inv, nbr_d, bu_d, bv_d;
+    std::vector<uint32_t> bid_d;
+    if (s.topo != KA_CUBIC) {
+      ka::bfs_order(s.N, s.z, c->host.nbr.data(), perm, inv);
+      ka::relabel_tables(c->host, s.z, perm, nbr_d, bu_d, bv_d, bid_d);
+      c->g.perm = (const int32_t*)(base + l.perm);
+      c->pl.inv = (const int32_t*)(base + l.inv);
+    } else {
+      nbr_d = c->host.nbr;
+      bu_d = c->host.bu;
+      bv_d = c->host.bv;
+      bid_d.assign(c->host.bid.begin(), c->host.bid.end());
+    }
+    cudaError_t e = cudaMemcpyAsync((void*)c->g.nbr, nbr_d.data(), nbr_d.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaMemcpyAsync((void*)c->g.bu, bu_d.data(), bu_d.size() * 4,
                                 cudaMemcpyHostToDevice, c->stream);
-    if (!e) e = cudaMemcpyAsync((void*)c->g.bv, c->host.bv.data(), c->host.bv.size() * 4,
+    if (!e) e = cudaMemcpyAsync((void*)c->g.bv, bv_d.data(), bv_d.size() * 4,
                                 cudaMemcpyHostToDevice, c->stream);
-    if (!e) e = cudaMemcpyAsync((void*)c->g.bid, bid32.data(), bid32.size() * 4,
+    if (!e) e = cudaMemcpyAsync((void*)c->g.bid, bid_d.data(), bid_d.size() * 4,
                                 cudaMemcpyHostToDevice, c->stream);
+    if (!e && c->g.perm)
+      e = cudaMemcpyAsync((void*)c->g.perm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice,
+                          c->stream);
+    if (!e && c->pl.inv)
+      e = cudaMemcpyAsync((void*)c->pl.inv, inv.data(), inv.size() * 4, cudaMemcpyHostToDevice,
+                          c->stream);
     if (!e) e = cudaStreamSynchronize(c->stream);
     if (e) {
       if (owns) cudaFree(buf);
@@ -449,7 +476,8 @@ ka_status ka_get_state(ka_ctx* c, uint64_t* n, uint64_t* n0, uint64_t* p) {
     if (!dst[k]) continue;
     const uint64_t* from = src[k];
     if (c->stage) {
-      e = ka::launch_to_canonical(src[k], c->stage, c->N, c->pl.P, c->pl.V, c->pl.xs, c->stream);
+      e = ka::launch_to_canonical(src[k], c->stage, c->N, c->pl.P, c->pl.V, c->pl.xs, c->pl.inv,
+                                  c->stream);
       from = c->stage;
     }
     // stream order keeps the next conversion from overwriting the staging
@@ -480,7 +508,8 @@ ka_status set_state_impl(ka_ctx* c, const uint64_t* n, const uint64_t* n0, const
       // before the conversion has read it
       e = cudaMemcpyAsync(c->stage, src[k], bytes, cudaMemcpyHostToDevice, c->stream);
       if (!e)
-        e = ka::launch_to_device(c->stage, dst[k], c->N, c->pl.P, c->pl.V, c->pl.xs, c->stream);
+        e = ka::launch_to_device(c->stage, dst[k], c->N, c->pl.P, c->pl.V, c->pl.xs, c->pl.inv,
+                                 c->stream);
     } else {
       e = cudaMemcpyAsync(dst[k], src[k], bytes, cudaMemcpyHostToDevice, c->stream);
     }

@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(256) k_init_mark(const InitArgs a, Planes pl) 
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int q = blockIdx.y;
   if (e >= a.N * V) return;
-  const int64_t i = canon_site(pl.xs, e / V);  // canonical site held at this position
+  const int64_t i = canon_pos(pl.inv, pl.xs, e / V);  // canonical site held at this position
   const int w = q * V + (int)(e % V);  // word index, replicas 64w .. 64w+63
   uint64_t word = 0;
   for (int j = 0; j < 32; ++j) {

@@ -91,6 +91,17 @@ struct Topology {
 std::string build_cubic_tables(int d, int L, Topology& t);
 std::string build_rrg(int64_t N, int z, uint64_t graph_seed, Topology& t);
 std::string build_graph(int64_t N, int z, const int32_t* nbr, Topology& t);
+// Storage order of a graph's sites: breadth-first from site 0 (then from the
+// lowest unvisited site), neighbours in row order.  perm[i] = position of
+// canonical site i, inv[q] = canonical site at position q.
+void bfs_order(int64_t N, int z, const int32_t* nbr, std::vector<int32_t>& perm,
+               std::vector<int32_t>& inv);
+// Device tables in storage positions: the neighbour rows relabelled (slot
+// order kept), and every class's bonds relabelled and sorted by their lower
+// position, each keeping its canonical bond id.
+void relabel_tables(const Topology& t, int z, const std::vector<int32_t>& perm,
+                    std::vector<int32_t>& nbr, std::vector<int32_t>& bu, std::vector<int32_t>& bv,
+                    std::vector<uint32_t>& bid);
 // Neighbour rows [M L^d][2d] of the layered random graph (section 5.2).
 std::string build_layered(int d, int L, int M, uint64_t graph_seed, int32_t* nbr);
 
@@ -106,6 +117,7 @@ struct Planes {
   int V;  // words per site per plane (1, 2 or 4)
   int P;  // planes (W / V)
   int xs; // side L of the split-row site order (below), or 0: sites in index order
+  const int32_t* inv = nullptr;  // graphs: canonical site at each storage position (device)
   KA_HD size_t plane_elems() const { return (size_t)N * V; }
 };
 
@@ -127,6 +139,14 @@ KA_HD int64_t canon_site(int xs, int64_t q) {
 }
 // split-row order used by a cubic pencil context of dimension d and side L
 KA_HD int split_side(int d, int L) { return d >= 2 ? L : 0; }
+
+// Graphs store sites in breadth-first order (a permutation built at context
+// creation, ka_topology.cu), so that sites that are close in the graph share
+// 32-byte sectors; inv maps a storage position back to its canonical site.
+// Canonical site of storage position q in either order (device code):
+KA_HD int64_t canon_pos(const int32_t* inv, int xs, int64_t q) {
+  return inv ? (int64_t)inv[q] : canon_site(xs, q);
+}
 
 // Warps per CTA of the cubic pencil kernel: a tile holds kCubicWarps / V
 // active pencils (one warp per pencil-word in the compute phase).
@@ -177,6 +197,7 @@ struct GraphDev {
   const int32_t* bu;
   const int32_t* bv;
   const uint32_t* bid;
+  const int32_t* perm;  // graphs: storage position of every canonical site (null: identity)
   int z, m;
   int cubic_L;  // > 0: the bonds are those of a cubic lattice of this side (its gate stream)
 };
@@ -219,9 +240,9 @@ cudaError_t launch_init(const Planes& pl, const InitScratch& s, int R, int64_t K
 
 // canonical [W][N] <-> device [P][N][V] (sites in the plane order of xs)
 cudaError_t launch_to_device(const uint64_t* canonical, uint64_t* device_layout, int64_t N, int P,
-                             int V, int xs, cudaStream_t st);
+                             int V, int xs, const int32_t* inv, cudaStream_t st);
 cudaError_t launch_to_canonical(const uint64_t* device_layout, uint64_t* canonical, int64_t N,
-                                int P, int V, int xs, cudaStream_t st);
+                                int P, int V, int xs, const int32_t* inv, cudaStream_t st);
 
 // Group kernels of three-dimensional lattices (ka_cubic_stream.cu): one-word
 // planes in split-row order, L in {32, 64, 128}.

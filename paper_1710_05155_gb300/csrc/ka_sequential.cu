@@ -47,6 +47,7 @@ struct SeqArgs {
   int64_t N;
   int z, d, L, V;
   int xs;  // split-row order of the planes (0: index order)
+  const int32_t* perm;  // graphs: storage position of every canonical site (nbr in positions)
   size_t plane_elems;
   uint32_t t0;
   int nsweeps;
@@ -134,8 +135,9 @@ __global__ void __launch_bounds__(32) k_sequential(const __grid_constant__ SeqAr
   int64_t st = a.V;
   if constexpr (SMEM) {
     // shared memory holds the word's planes in site index order
+    // (graphs: storage order, the labels the neighbour table uses)
     for (int64_t i = lane; i < a.N; i += 32) {
-      const int64_t g = dev_site(a.xs, i) * a.V;
+      const int64_t g = (a.perm ? i : dev_site(a.xs, i)) * a.V;
       sm[i] = gn[g];
       sm[a.N + i] = gp[g];
     }
@@ -145,7 +147,9 @@ __global__ void __launch_bounds__(32) k_sequential(const __grid_constant__ SeqAr
     st = 1;
   }
   // element of site i in n and p
-  auto at = [&](uint32_t i) -> int64_t { return SMEM ? (int64_t)i : dev_site(a.xs, i) * st; };
+  auto at = [&](uint32_t i) -> int64_t {
+    return SMEM ? (int64_t)i : (a.perm ? (int64_t)i : dev_site(a.xs, i)) * st;
+  };
   uint32_t* stamp = reinterpret_cast<uint32_t*>(sm + (SMEM ? 2 * a.N : 0));
   const uint32_t hm = a.hmask;
   for (uint32_t b = lane; b <= hm; b += 32) stamp[b] = 0;
@@ -158,8 +162,10 @@ __global__ void __launch_bounds__(32) k_sequential(const __grid_constant__ SeqAr
       const int64_t k = k0 + lane;
       const bool live = k < a.N;
       const uint64_t r = live ? draw_bond(a.rk, t, (uint32_t)k, w, range) : 0ull;
-      // this lane's bond (i, j) and the neighbours of both
-      const uint32_t i = (uint32_t)(r / (uint64_t)a.z);
+      // this lane's bond (i, j) and the neighbours of both: drawn by
+      // canonical site and slot, then (graphs) followed in storage positions
+      uint32_t i = (uint32_t)(r / (uint64_t)a.z);
+      if (a.perm && live) i = (uint32_t)a.perm[i];
       const int sel = (int)(r % (uint64_t)a.z);
       uint32_t ni_[8], nj_[8];
       neighbours(a, i, ni_);
@@ -217,7 +223,7 @@ __global__ void __launch_bounds__(32) k_sequential(const __grid_constant__ SeqAr
   if constexpr (SMEM) {
     __syncwarp();
     for (int64_t i = lane; i < a.N; i += 32) {
-      const int64_t g = dev_site(a.xs, i) * a.V;
+      const int64_t g = (a.perm ? i : dev_site(a.xs, i)) * a.V;
       gn[g] = sm[i];
       gp[g] = sm[a.N + i];
     }
@@ -285,6 +291,7 @@ extern "C" ka_status ka_sweep_sequential(ka_ctx* c, int64_t nsweeps) {
   a.L = c->L;
   a.V = c->pl.V;
   a.xs = c->pl.xs;
+  a.perm = c->g.perm;
   a.plane_elems = c->pl.plane_elems();
   a.rk = c->rk;
   const unsigned words = (unsigned)(c->R / 64);

@@ -365,3 +365,57 @@ extern "C" ka_status ka_layered_graph(int32_t d, int32_t L, int32_t M, uint64_t 
   if (!nbr) return KA_EINVAL;
   return ka::build_layered(d, L, M, graph_seed, nbr).empty() ? KA_OK : KA_EINVAL;
 }
+
+namespace ka {
+
+void bfs_order(int64_t N, int z, const int32_t* nbr, std::vector<int32_t>& perm,
+               std::vector<int32_t>& inv) {
+  perm.assign((size_t)N, -1);
+  inv.assign((size_t)N, 0);
+  int64_t head = 0, tail = 0;  // inv doubles as the queue
+  for (int64_t root = 0; root < N; ++root) {
+    if (perm[root] >= 0) continue;
+    perm[root] = (int32_t)tail;
+    inv[tail++] = (int32_t)root;
+    while (head < tail) {
+      const int32_t x = inv[head++];
+      for (int k = 0; k < z; ++k) {
+        const int32_t y = nbr[(int64_t)x * z + k];
+        if (perm[y] < 0) {
+          perm[y] = (int32_t)tail;
+          inv[tail++] = y;
+        }
+      }
+    }
+  }
+}
+
+void relabel_tables(const Topology& t, int z, const std::vector<int32_t>& perm,
+                    std::vector<int32_t>& nbr, std::vector<int32_t>& bu, std::vector<int32_t>& bv,
+                    std::vector<uint32_t>& bid) {
+  const int64_t N = (int64_t)perm.size();
+  nbr.resize(t.nbr.size());
+  for (int64_t x = 0; x < N; ++x)
+    for (int k = 0; k < z; ++k)
+      nbr[(int64_t)perm[x] * z + k] = perm[t.nbr[(int64_t)x * z + k]];
+  const size_t E = t.bu.size();
+  bu.resize(E);
+  bv.resize(E);
+  bid.resize(E);
+  std::vector<std::pair<int32_t, int64_t>> key;
+  for (int64_t c = 0; c + 1 < (int64_t)t.class_off.size(); ++c) {
+    const int64_t a = t.class_off[c], b = t.class_off[c + 1];
+    key.clear();
+    for (int64_t e = a; e < b; ++e)
+      key.emplace_back(std::min(perm[t.bu[e]], perm[t.bv[e]]), e);
+    std::sort(key.begin(), key.end());
+    for (int64_t k = 0; k < b - a; ++k) {
+      const int64_t e = key[k].second;
+      bu[a + k] = perm[t.bu[e]];
+      bv[a + k] = perm[t.bv[e]];
+      bid[a + k] = (uint32_t)t.bid[e];
+    }
+  }
+}
+
+}  // namespace ka
