@@ -124,7 +124,10 @@ typedef struct {
     int64_t sweep;      /* sweeps completed since init (or set_state) */
     int64_t K;          /* particles per replica at the last init (-1 if none) */
     uint64_t seed;      /* dynamics seed */
-    int32_t kernel;     /* 0 = cubic pencil kernel, 1 = edge-gather kernel */
+    int32_t kernel;     /* 0 = general cubic pencil kernel, 1 = edge-gather kernel,
+                           3 = group kernels of three-dimensional lattices (d = 3,
+                           L % 4 == 0, L <= 128: from two planes up, or one
+                           plane with L in {32, 64, 128} or L >= 96, L % 8 == 0) */
     int32_t rrg_attempts; /* configuration-model attempts (KA_RRG) */
     size_t device_bytes;  /* device memory the context uses */
     int32_t planes;       /* device state planes per array */

@@ -397,7 +397,7 @@ ka_status ka_sweep(ka_ctx* c, int64_t n) {
   if (n == 0) return KA_OK;
   DeviceGuard dg(c->device);
   cudaError_t e = cudaSuccess;
-  if (c->pencil && ka::stream_supported(c->d, c->L)) {
+  if (c->pencil && ka::stream_preferred(c->d, c->L, c->pl.P)) {
     // plane-outer order keeps the planes of one launch resident in the L2
     // across sweeps
     const int nq = ka::stream_planes_per_launch(c->L, c->pl.P);
@@ -560,13 +560,14 @@ ka_status ka_info(const ka_ctx* c, ka_info_t* out) {
   out->sweep = c->sweep;
   out->K = c->K;
   out->seed = c->seed;
-  out->kernel = c->pencil ? 0 : 1;
+  out->kernel = !c->pencil ? 1 : ka::stream_preferred(c->d, c->L, c->pl.P) ? 3 : 0;
   out->rrg_attempts = c->host.attempts;
   out->device_bytes = c->bytes;
   out->planes = c->pl.P;
   out->plane_words = c->pl.V;
   out->planes_per_launch =
-      (c->pencil && ka::stream_supported(c->d, c->L)) ? ka::stream_planes_per_launch(c->L, c->pl.P) : 1;
+      (c->pencil && ka::stream_preferred(c->d, c->L, c->pl.P)) ? ka::stream_planes_per_launch(c->L, c->pl.P)
+                                                                : 1;
   return KA_OK;
 }
 

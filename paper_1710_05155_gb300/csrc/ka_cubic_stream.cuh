@@ -1,5 +1,12 @@
-// ka_cubic_stream.cuh -- group kernels for three-dimensional lattices of side
-// L in {32, 64, 128} stored one word per site and plane in split-row order.
+// ka_cubic_stream.cuh -- group kernels for three-dimensional lattices (any
+// side L with L % 4 == 0, 4 <= L <= 128) stored one word per site and plane
+// in split-row order.  The sides 32, 64 and 128 run kernels with the side
+// fixed at compile time (k_rows, k_pencils); every other side runs the same
+// algorithm with the geometry read from the launch arguments (k_rows_any,
+// k_pencils_any: partial warps of rows, blocks of fewer pencils with several
+// layers per warp, chunks of unequal length along the pencils).  The two
+// forms are kept apart because the general form, instantiated for a fixed
+// side, ran 6 % slower at L = 128 (33.6 against 31.6 us per word-sweep).
 //
 // One launch runs one bond-class group (mu, par) -- the four classes
 // c = 4(2 mu + par) + a, a = 0..3 -- on one or more one-word state planes
@@ -56,16 +63,19 @@ struct Args {
   uint64_t* p;
   size_t plane;     // elements per plane
   int nplanes;      // planes of this launch
+  int L;            // side (read by the general form)
   int mu, par;
   uint32_t t, cls0, word0;
   RoundKeys rk;
 };
 
+// L = the side at compile time, or 0: the general form, side from the arguments
 template <int L>
 cudaError_t launch_l(const Args& a, int m, cudaStream_t st);
 
 #define KA_STREAM_EXTERN(LL) \
   extern template cudaError_t launch_l<LL>(const Args&, int, cudaStream_t);
+KA_STREAM_EXTERN(0)
 KA_STREAM_EXTERN(32)
 KA_STREAM_EXTERN(64)
 KA_STREAM_EXTERN(128)
@@ -426,10 +436,337 @@ cudaError_t launch_pencils(const Args& a, cudaStream_t st) {
                    : cudaLaunchKernelEx(&cfg, k_pencils<L, M, 2>, a);
 }
 
+// Geometry of the mu = 0 launch: a row of L sites is S = L / 4 segments
+// (one per lane), PW = 32 / S rows per warp (lanes beyond PW S idle), and a
+// CTA's eight warps take the 4 PW active rows of each of two layers in a
+// block of Ty = 8 PW consecutive y (rows past L idle).
+struct RowGeo {
+  int L, S, PW, Ty, nyb;
+  __device__ __host__ __forceinline__ explicit RowGeo(int L_) : L(L_) {
+    S = L / 4;
+    PW = 32 / S;
+    Ty = 8 * PW;
+    nyb = (L + Ty - 1) / Ty;
+  }
+};
+
+// Geometry of the mu > 0 launches: NP pencils per warp and layer (the
+// largest power of two up to 32 that divides L / 2, so blocks of pencils
+// tile a half-row exactly), PL = 32 / NP layers per warp (layers past L
+// idle), NS = L / 4 segments per pencil cut into chunks of J consecutive
+// segments, one chunk per warp (CW warps of the eight carry a chunk).
+struct PencilGeo {
+  int L, Lh, NP, PL, nhb, nsg, NS, J, CW;
+  __device__ __host__ __forceinline__ explicit PencilGeo(int L_) : L(L_) {
+    Lh = L / 2;
+    NP = Lh & -Lh;
+    if (NP > 32) NP = 32;
+    PL = 32 / NP;
+    nhb = Lh / NP;
+    nsg = (L + PL - 1) / PL;
+    NS = L / 4;
+    J = (NS + 7) / 8;
+    CW = (NS + J - 1) / J;
+  }
+};
+
+// General form of k_rows (below): the same work with the geometry of RowGeo.
+template <int M>
+__global__ void __launch_bounds__(32 * kRowWarps) k_rows_any(const __grid_constant__ Args a) {
+  const RowGeo G(a.L);
+  const int L = G.L, S = G.S, PW = G.PW, Ty = G.Ty, nyb = G.nyb, Lh = L / 2;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t b = blockIdx.x;
+  const int yb = (int)(b % (uint32_t)nyb);
+  b /= (uint32_t)nyb;
+  const int zp = (int)(b % (uint32_t)(L / 2));
+  const int plane = (int)(b / (uint32_t)(L / 2));
+  const int z = 2 * zp + warp / (kRowWarps / 2);
+  const int gj = lane / S, seg = lane - gj * S;
+  const bool in_row = gj < PW;
+  const int prev = in_row ? gj * S + (seg == 0 ? S - 1 : seg - 1) : lane;
+  const int next = in_row ? gj * S + (seg == S - 1 ? 0 : seg + 1) : lane;
+  const int i = (warp % (kRowWarps / 2)) * PW + gj;  // active row of this layer in the block
+  const int y = yb * Ty + 2 * i + ((a.par ^ z) & 1);
+  const bool live = in_row && y < L;
+  // gate blocks (independent of the state: first)
+  const uint32_t site =
+      (uint32_t)(4 * seg) + (uint32_t)L * ((uint32_t)y + (uint32_t)L * (uint32_t)z);
+  const uint32_t word = a.word0 + (uint32_t)plane;
+  const uint4 g01 = philox(make_uint4(a.t, a.cls0, site, word), a.rk);
+  const uint4 g23 = philox(make_uint4(a.t, a.cls0 + 2, site + 2, word), a.rk);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  uint64_t* n = a.n + (size_t)plane * a.plane;
+  uint64_t* p = a.p + (size_t)plane * a.plane;
+  auto row = [&](int yy, int zz) -> size_t { return ((size_t)zz * L + yy) * (size_t)L; };
+  const ulonglong2* cn = reinterpret_cast<const ulonglong2*>(n);
+  const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(p);
+  const ulonglong2 zero = make_ulonglong2(0ull, 0ull);
+  // chunk indices (16 bytes): even sites of the segment at seg, odd ones at Lh / 2 + seg
+  size_t e0 = 0, o0 = 0;
+  ulonglong2 ne = zero, no = zero, pe = zero, po = zero, q[4][2];
+  if (live) {
+    const size_t r0 = row(y, z);
+    e0 = r0 / 2 + seg;
+    o0 = r0 / 2 + Lh / 2 + seg;
+    const size_t nb[4] = {row(y == L - 1 ? 0 : y + 1, z) / 2, row(y == 0 ? L - 1 : y - 1, z) / 2,
+                          row(y, z == L - 1 ? 0 : z + 1) / 2, row(y, z == 0 ? L - 1 : z - 1) / 2};
+    ne = cn[e0];
+    no = cn[o0];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      q[k][0] = __ldg(cn + nb[k] + seg);
+      q[k][1] = __ldg(cn + nb[k] + Lh / 2 + seg);
+    }
+    pe = cp[e0];
+    po = cp[o0];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k][0] = q[k][1] = zero;
+  }
+  // sites 4 seg + k: even ones in the first half (k = 0, 2), odd ones in the second
+  uint64_t nn[4] = {ne.x, no.x, ne.y, no.y}, mA[4], mB[4], fl[4];
+  masks4<M>(q[0][0].x, q[1][0].x, q[2][0].x, q[3][0].x, mA[0], mB[0]);
+  masks4<M>(q[0][0].y, q[1][0].y, q[2][0].y, q[3][0].y, mA[2], mB[2]);
+  masks4<M>(q[0][1].x, q[1][1].x, q[2][1].x, q[3][1].x, mA[1], mB[1]);
+  masks4<M>(q[0][1].y, q[1][1].y, q[2][1].y, q[3][1].y, mA[3], mB[3]);
+  run_chain(nn, mA, mB, fl, g01, g23, prev, next);
+  if (live) {
+    ulonglong2* gn = reinterpret_cast<ulonglong2*>(n);
+    ulonglong2* gp = reinterpret_cast<ulonglong2*>(p);
+    gn[e0] = make_ulonglong2(nn[0], nn[2]);
+    gn[o0] = make_ulonglong2(nn[1], nn[3]);
+    gp[e0] = make_ulonglong2(pe.x & ~fl[0], pe.y & ~fl[2]);
+    gp[o0] = make_ulonglong2(po.x & ~fl[1], po.y & ~fl[3]);
+  }
+}
+
+template <int M>
+cudaError_t launch_rows_any(const Args& a, cudaStream_t st) {
+  const RowGeo G(a.L);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.nplanes * (G.L / 2) * G.nyb));
+  cfg.blockDim = dim3(32 * kRowWarps);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_rows_any<M>, a);
+}
+
+// General form of k_pencils (below): NP pencils of PL layers per warp, CW
+// chunks of J segments along the pencils (the last may be shorter), the
+// chunk ring closed over those CW chunks.
+template <int M, int MU>
+__global__ void __launch_bounds__(32 * kPencilWarps) k_pencils_any(const __grid_constant__ Args a) {
+  const PencilGeo G(a.L);
+  const int L = G.L, Lh = G.Lh, NP = G.NP, PL = G.PL, nhb = G.nhb, J = G.J, CW = G.CW;
+  // rows (t, s) start at (s L + t) L (mu = 1) or (t L + s) L (mu = 2): the
+  // word strides of one step along the pencil and across layers
+  const size_t TS = (MU == 1) ? (size_t)L : (size_t)L * L;
+  const size_t SS = (MU == 1) ? (size_t)L * L : (size_t)L;
+  const uint32_t CT = (MU == 1) ? (uint32_t)L : (uint32_t)(L * L);  // canonical site steps
+  const uint32_t CS = (MU == 1) ? (uint32_t)(L * L) : (uint32_t)L;
+  __shared__ uint64_t xn[kPencilWarps][32], xok[kPencilWarps][32], xsw[kPencilWarps][32];
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t b = blockIdx.x;
+  const int hb = (int)(b % (uint32_t)nhb);
+  b /= (uint32_t)nhb;
+  const int sgrp = (int)(b % (uint32_t)G.nsg);
+  const int plane = (int)(b / (uint32_t)G.nsg);
+  const int s = sgrp * PL + lane / NP;
+  const int h = hb * NP + lane % NP;
+  const bool live = s < L;  // layers past L (when PL does not divide L) idle
+  // this warp's chunk: segments j0 .. j0 + nseg - 1; warps past CW carry none
+  const int j0 = warp * J;
+  const int nseg = warp < CW ? min(J, G.NS - j0) : 0;
+  const int act = (a.par ^ s) & 1, oth = act ^ 1;
+  const uint32_t x = 2u * (uint32_t)h + (uint32_t)act;  // canonical x of this lane's pencil
+  // x neighbours, in the other half: odd[h - 1], odd[h] (x even) or even[h], even[h + 1] (x odd)
+  const int hl = act == 0 ? (h == 0 ? Lh - 1 : h - 1) : h;
+  const int hr = act == 0 ? h : (h == Lh - 1 ? 0 : h + 1);
+  const int sm = s == 0 ? L - 1 : s - 1, sp = s >= L - 1 ? 0 : s + 1;
+  const int t0 = 4 * j0;
+  // position t0 of this lane's pencil, its x neighbours and its neighbours
+  // across the layers (same x: the other half of layers s -/+ 1)
+  uint64_t* const n = a.n + (size_t)plane * a.plane + (size_t)t0 * TS;
+  uint64_t* const p = a.p + (size_t)plane * a.plane + (size_t)t0 * TS;
+  uint64_t* const gn = n + (size_t)s * SS + (size_t)act * Lh + h;
+  uint64_t* const gp = p + (size_t)s * SS + (size_t)act * Lh + h;
+  const uint64_t* const gl = n + (size_t)s * SS + (size_t)oth * Lh + hl;
+  const uint64_t* const gr = n + (size_t)s * SS + (size_t)oth * Lh + hr;
+  const uint64_t* const gm = n + (size_t)sm * SS + (size_t)act * Lh + h;
+  const uint64_t* const gq = n + (size_t)sp * SS + (size_t)act * Lh + h;
+  const bool mem = live && nseg > 0;  // this lane touches memory
+  const uint32_t word = a.word0 + (uint32_t)plane;
+  const uint32_t site0 = x + (uint32_t)t0 * CT + (uint32_t)s * CS;  // canonical site of t0
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  // the previous chunk's last site at the start of the group
+  uint64_t left0 = 0;
+  if (mem) left0 = (t0 == 0) ? gn[(size_t)(L - 1) * TS] : gn[-(ptrdiff_t)TS];
+  uint64_t qn[4], qf[4], qp[4], qA2 = 0, qB2 = 0, qA3 = 0, qB3 = 0;  // segment j - 1
+  uint4 qg23 = make_uint4(0, 0, 0, 0);
+  uint64_t s0n = 0, s0f = 0, s0p = 0;  // the chunk's first site, stored last
+#pragma unroll
+  for (int k = 0; k < 4; ++k) qn[k] = qf[k] = qp[k] = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {  // J <= 4 for L <= 128
+    if (j >= nseg) break;
+    uint64_t cn[4], cp[4], cA[4], cB[4], cf[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const size_t o = (size_t)(4 * j + k) * TS;
+      if (mem) {
+        cn[k] = gn[o];
+        cp[k] = gp[o];
+        masks4<M>(__ldg(gl + o), __ldg(gr + o), __ldg(gm + o), __ldg(gq + o), cA[k], cB[k]);
+      } else {
+        cn[k] = cp[k] = 0;
+        masks4<M>(0, 0, 0, 0, cA[k], cB[k]);
+      }
+    }
+    const uint32_t st = site0 + (uint32_t)(4 * j) * CT;
+    const uint4 g01 = philox(make_uint4(a.t, a.cls0, st, word), a.rk);
+    const uint4 g23 = philox(make_uint4(a.t, a.cls0 + 2, st + 2u * CT, word), a.rk);
+    // class 0: bond (c0, c1); c0's other along-neighbour is site 4j - 1 at its group-start value
+    {
+      const uint64_t left = (j == 0) ? left0 : qn[3];
+      const uint64_t sw = (cn[0] ^ cn[1]) & lo64(g01) & okmask(left, cA[0], cB[0]) &
+                          okmask(cn[2], cA[1], cB[1]);
+      cn[0] ^= sw;
+      cn[1] ^= sw;
+      cf[0] = sw;
+      cf[1] = sw;
+    }
+    // class 1: bond (c1, c2); other along-neighbours c0 and c3
+    {
+      const uint64_t sw = (cn[1] ^ cn[2]) & hi64(g01) & okmask(cn[0], cA[1], cB[1]) &
+                          okmask(cn[3], cA[2], cB[2]);
+      cn[1] ^= sw;
+      cn[2] ^= sw;
+      cf[1] |= sw;
+      cf[2] = sw;
+    }
+    cf[3] = 0;
+    if (j == 0) {
+      // what the previous chunk's classes 2 and 3 need of this chunk's first site
+      xn[warp][lane] = cn[0];
+      xok[warp][lane] = okmask(cn[1], cA[0], cB[0]);
+    } else {
+      // class 2 of segment j - 1: bond (q2, q3); q3's other along-neighbour is c0
+      {
+        const uint64_t sw = (qn[2] ^ qn[3]) & lo64(qg23) & okmask(qn[1], qA2, qB2) &
+                            okmask(cn[0], qA3, qB3);
+        qn[2] ^= sw;
+        qn[3] ^= sw;
+        qf[2] |= sw;
+        qf[3] |= sw;
+      }
+      // class 3 of segment j - 1: bond (q3, c0); c0's other along-neighbour is c1
+      {
+        const uint64_t sw = (qn[3] ^ cn[0]) & hi64(qg23) & okmask(qn[2], qA3, qB3) &
+                            okmask(cn[1], cA[0], cB[0]);
+        qn[3] ^= sw;
+        qf[3] |= sw;
+        cn[0] ^= sw;
+        cf[0] |= sw;
+      }
+      // segment j - 1 is final (its first site waits if it is the chunk's first)
+      if (mem) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (k == 0 && j == 1) continue;
+          const size_t o = (size_t)(4 * (j - 1) + k) * TS;
+          gn[o] = qn[k];
+          gp[o] = qp[k] & ~qf[k];
+        }
+      }
+    }
+    if (j == 0) {
+      s0n = cn[0];
+      s0f = cf[0];
+      s0p = cp[0];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      qn[k] = cn[k];
+      qf[k] = cf[k];
+      qp[k] = cp[k];
+    }
+    qA2 = cA[2];
+    qB2 = cB[2];
+    qA3 = cA[3];
+    qB3 = cB[3];
+    qg23 = g23;
+  }
+  __syncthreads();
+  // classes 2 and 3 of the last segment, with the next chunk's first site
+  if (nseg > 0) {
+    const int wn = warp == CW - 1 ? 0 : warp + 1;
+    const uint64_t nx = xn[wn][lane], okn = xok[wn][lane];
+    uint64_t sw = (qn[2] ^ qn[3]) & lo64(qg23) & okmask(qn[1], qA2, qB2) & okmask(nx, qA3, qB3);
+    qn[2] ^= sw;
+    qn[3] ^= sw;
+    qf[2] |= sw;
+    qf[3] |= sw;
+    sw = (qn[3] ^ nx) & hi64(qg23) & okmask(qn[2], qA3, qB3) & okn;
+    qn[3] ^= sw;
+    qf[3] |= sw;
+    xsw[warp][lane] = sw;
+    if (mem) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (k == 0 && nseg == 1) continue;
+        const size_t o = (size_t)(4 * (nseg - 1) + k) * TS;
+        gn[o] = qn[k];
+        gp[o] = qp[k] & ~qf[k];
+      }
+    }
+  }
+  __syncthreads();
+  // the chunk's first site, after the previous chunk's class-3 bond
+  if (nseg > 0 && mem) {
+    const uint64_t in = xsw[warp == 0 ? CW - 1 : warp - 1][lane];
+    gn[0] = s0n ^ in;
+    gp[0] = s0p & ~(s0f | in);
+  }
+}
+
+template <int M>
+cudaError_t launch_pencils_any(const Args& a, cudaStream_t st) {
+  const PencilGeo G(a.L);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.nplanes * G.nsg * G.nhb));
+  cfg.blockDim = dim3(32 * kPencilWarps);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return a.mu == 1 ? cudaLaunchKernelEx(&cfg, k_pencils_any<M, 1>, a)
+                   : cudaLaunchKernelEx(&cfg, k_pencils_any<M, 2>, a);
+}
+
 }  // namespace
 
 template <int L>
 cudaError_t launch_l(const Args& a, int m, cudaStream_t st) {
+#define KA_M_CASES_ANY(FN)                     \
+  switch (m < 5 ? m : 5) {                     \
+    case 0: return FN<0>(a, st);               \
+    case 1: return FN<1>(a, st);               \
+    case 2: return FN<2>(a, st);               \
+    case 3: return FN<3>(a, st);               \
+    case 4: return FN<4>(a, st);               \
+    default: return FN<5>(a, st);              \
+  }
 #define KA_M_CASES(FN)                         \
   switch (m < 5 ? m : 5) {                     \
     case 0: return FN<L, 0>(a, st);            \
@@ -439,9 +776,15 @@ cudaError_t launch_l(const Args& a, int m, cudaStream_t st) {
     case 4: return FN<L, 4>(a, st);            \
     default: return FN<L, 5>(a, st);           \
   }
-  if (a.mu == 0) KA_M_CASES(launch_rows)
-  KA_M_CASES(launch_pencils)
+  if constexpr (L == 0) {
+    if (a.mu == 0) KA_M_CASES_ANY(launch_rows_any)
+    KA_M_CASES_ANY(launch_pencils_any)
+  } else {
+    if (a.mu == 0) KA_M_CASES(launch_rows)
+    KA_M_CASES(launch_pencils)
+  }
 #undef KA_M_CASES
+#undef KA_M_CASES_ANY
 }
 #endif  // KA_STREAM_INSTANCES
 

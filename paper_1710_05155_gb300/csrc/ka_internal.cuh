@@ -245,8 +245,10 @@ cudaError_t launch_to_canonical(const uint64_t* device_layout, uint64_t* canonic
                                 int P, int V, int xs, const int32_t* inv, cudaStream_t st);
 
 // Group kernels of three-dimensional lattices (ka_cubic_stream.cu): one-word
-// planes in split-row order, L in {32, 64, 128}.
+// planes in split-row order, d = 3, L % 4 == 0, L <= 128.
 bool stream_supported(int d, int L);
+// whether a context of P one-word planes runs them (else the general kernel)
+bool stream_preferred(int d, int L, int P);
 // planes one launch of these kernels takes
 int stream_planes_per_launch(int L, int P);
 // Group (mu, par) of sweep t on planes q0 .. q0 + nq - 1.

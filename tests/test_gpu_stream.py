@@ -1,6 +1,9 @@
-"""GPU parity of the group kernels of three-dimensional lattices (L in {32, 64, 128}).
+"""GPU parity of the group kernels of three-dimensional lattices (L % 4 == 0, L <= 128).
 
-These kernels run every sweep of three-dimensional lattices of those sides;
+These kernels run every sweep of three-dimensional lattices of those sides
+(32, 64 and 128 with the side fixed at compile time, every other side with the
+geometry read at run time: partial warps of rows, blocks of fewer pencils and
+several layers per warp, chunks of unequal length along the pencils);
 planes hold one 64-replica word per site in split-row order (even x, then odd
 x, in every row), which get_state / set_state translate.  Integer work, so
 every compared word must equal the oracle's.  The cases cover one to five
@@ -38,7 +41,7 @@ def _assert_same(sim, st, what=""):
 def _run(L, m, R, seed, rho, sweeps, per_call=1):
     topo = O.cubic(3, L)
     sim = K.Simulation(topo=K.KA_CUBIC, d=3, L=L, m=m, replicas=R)
-    assert sim.info["kernel"] == 0 and sim.info["plane_words"] == 1 and sim.info["planes"] == R // 64
+    assert sim.info["kernel"] == 3 and sim.info["plane_words"] == 1 and sim.info["planes"] == R // 64
     sim.init(seed, rho)
     st = O.init(topo.N, R, seed, rho)
     _assert_same(sim, st, "after init")
@@ -72,6 +75,24 @@ def test_l32_sweeps_in_one_call():
 
 def test_l64_every_sweep():
     _run(64, 3, 128, seed=11, rho=0.8, sweeps=2)
+
+
+@pytest.mark.parametrize("L,m,R,sweeps", [
+    (4, 3, 128, 4), (8, 2, 128, 4), (12, 3, 192, 4), (16, 3, 192, 4), (20, 1, 128, 4),
+    (24, 4, 256, 3), (28, 3, 128, 3), (36, 3, 128, 2), (40, 5, 128, 2), (48, 3, 320, 2),
+    (52, 0, 128, 2), (60, 3, 192, 2), (80, 2, 128, 1), (96, 3, 64, 1), (100, 3, 128, 1),
+    (112, 4, 64, 1), (120, 3, 64, 1), (124, 3, 128, 1)])
+def test_runtime_side_every_sweep(L, m, R, sweeps):
+    # sides other than 32, 64, 128: the general form, geometry read at run time
+    # (from two planes up, or one plane from L = 96 up with L % 8 == 0)
+    _run(L, m, R, seed=100 + L, rho=0.8, sweeps=sweeps)
+
+
+def test_one_plane_small_sides_take_the_general_kernel():
+    for L in (80, 100):
+        sim = K.Simulation(topo=K.KA_CUBIC, d=3, L=L, m=3, replicas=64)
+        assert sim.info["kernel"] == 0
+        sim.close()
 
 
 def test_l128_one_plane():
