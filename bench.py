@@ -375,8 +375,9 @@ def run_batched_sample(dev: int, jobs_n: int, scale: float) -> dict:
     moves = float(sum(j.work for j in jobs))
     t0 = time.perf_counter()
     ms_b, rounds, k = _run_batch(jobs, K.KA_BATCH_GRAPH, dev, 0)
+    own = _run_batch.own_tiles
     ms_p, _, _ = _run_batch(jobs, K.KA_BATCH_PLAIN, dev, k)
-    return {"value": moves / (ms_b / 1000.0), "unit": UNIT,
+    return {"value": moves / (ms_b / 1000.0), "unit": UNIT, "own_launch_tiles": own,
             "workload": f"the first {jobs_n} of the 512-instance mix (cubic d=3 m=3 L in "
                         f"{{16..96}} or RRG z=4 m=2 N=2^12..2^18, R=64), sweeps x {scale}",
             "plain": moves / (ms_p / 1000.0), "ms": ms_b, "plain_ms": ms_p,
@@ -599,6 +600,7 @@ def _run_batch(jobs, flags, dev, k):
     rounds = 0
     if k == 0 and not (flags & K.KA_BATCH_PLAIN):
         k = b.autotune()  # times real rounds of this batch: part of the timed work
+    own_tiles = b.tuning()[1]
     while b.info()["active"]:
         b.step(k or 16)
         rounds += 1
@@ -606,6 +608,7 @@ def _run_batch(jobs, flags, dev, k):
     torch.cuda.synchronize(dev)
     ms = ev0.elapsed_time(ev1)
     b.close()
+    _run_batch.own_tiles = own_tiles
     return ms, rounds, k
 
 
@@ -626,7 +629,9 @@ def run_batched(args) -> None:
     clocks = ClockSampler(dev)
     clocks.start()
     ms_b, rounds, k = _run_batch(jobs, K.KA_BATCH_GRAPH, dev, args.round)
+    own = _run_batch.own_tiles
     ms_p, _, _ = _run_batch(jobs, K.KA_BATCH_PLAIN, dev, k)
+    _run_batch.own_tiles = own
     clk = clocks.stop()
     value = moves / (ms_b / 1000.0)
     line = {
@@ -636,7 +641,8 @@ def run_batched(args) -> None:
         "config": {"workload": f"{args.jobs} instances: cubic d=3 m=3 L in {{16..96}} or RRG "
                                f"z=4 m=2 N=2^12..2^18, R=64, rho U[0.75,0.88], sweeps "
                                f"U[1000,20000] x {args.sweep_scale}, observe every 100",
-                   "round_sweeps": k, "rounds": rounds, "site_replica_moves": moves},
+                   "round_sweeps": k, "own_launch_tiles": _run_batch.own_tiles,
+                   "rounds": rounds, "site_replica_moves": moves},
         "plain": {"value": moves / (ms_p / 1000.0), "unit": UNIT, "ms": ms_p},
         "batched_over_plain": ms_p / ms_b,
         "clocks": clk,

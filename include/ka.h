@@ -337,11 +337,23 @@ ka_status ka_batch_adopt(ka_batch *b, ka_ctx *ctx, const ka_job_spec *spec, int6
  * the due observations.  *sweeps_run = the round's length.  Synchronises. */
 ka_status ka_batch_step(ka_batch *b, int64_t max_sweeps, int64_t *sweeps_run);
 
-/* Time a few round lengths (4, 16, 64 sweeps) on the live batch and keep
- * the fastest for ka_batch_step(b, 0, ...).  Each length first runs warm-up
- * rounds (tables; in graph mode the capture), then one timed round; all
- * these rounds do real work.  *best_round may be NULL. */
+/* Tune the live batch by timing real rounds, in two stages: (1) which cubic
+ * jobs run with their own launches -- the tile threshold (one wave of
+ * tiles, half, a quarter, an eighth, or none on their own launches), at the
+ * present round length; (2) the round length (4, 16, 64 sweeps) with the
+ * chosen threshold.  Each candidate first runs warm-up rounds (tables; in
+ * graph mode the capture), then one timed round; all these rounds do real
+ * work.  The fastest of each stage is kept (ka_batch_tuning);
+ * *best_round = the round length, may be NULL.  Results do not depend on
+ * the tuning. */
 ka_status ka_batch_autotune(ka_batch *b, int64_t *best_round);
+
+/* The batch's present tuning: the round length ka_batch_step(b, 0, ...)
+ * takes, and the tile threshold above which a cubic job runs with its own
+ * launches inside each round instead of sharing the batched launches (in
+ * tiles of eight one-word pencils; before autotuning: one wave of tiles,
+ * twice the SM count).  Either pointer may be NULL. */
+ka_status ka_batch_tuning(const ka_batch *b, int64_t *round_sweeps, int64_t *own_tiles);
 
 /* Progress of a job. */
 ka_status ka_batch_poll(const ka_batch *b, int64_t job_id, int64_t *sweep, int32_t *finished);

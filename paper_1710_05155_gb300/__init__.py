@@ -92,6 +92,7 @@ _SIGS = {
     "ka_batch_autotune": (C.c_int, [C.c_void_p, _P(C.c_int64)]),
     "ka_batch_poll": (C.c_int, [C.c_void_p, C.c_int64, _P(C.c_int64), _P(C.c_int32)]),
     "ka_batch_state": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ka_batch_tuning": (C.c_int, [C.c_void_p, _P(C.c_int64), _P(C.c_int64)]),
     "ka_batch_observations": (C.c_int, [C.c_void_p, C.c_int64, _P(C.c_int64), C.c_void_p,
                                         C.c_void_p]),
     "ka_batch_remove": (C.c_int, [C.c_void_p, C.c_int64]),
@@ -406,6 +407,12 @@ class Batch:
         k = C.c_int64(0)
         _check(load().ka_batch_autotune(self.handle, C.byref(k)), "ka_batch_autotune")
         return k.value
+
+    def tuning(self):
+        """(round length, own-launch tile threshold) the batch uses now."""
+        k, t = C.c_int64(0), C.c_int64(0)
+        _check(load().ka_batch_tuning(self.handle, C.byref(k), C.byref(t)), "ka_batch_tuning")
+        return k.value, t.value
 
     def poll(self, job: int):
         t, f = C.c_int64(0), C.c_int32(0)

@@ -87,6 +87,9 @@ struct ka_batch {
   int64_t last_k = 0;  // a round length is captured the second time it is used
   int64_t tuned_k = 16;
   int64_t wave_tiles = 304;  // tiles one persistent launch of the pencil kernel runs at once
+  // cubic jobs whose groups have at least this many tiles of the batched
+  // pencil kernel run with their own launches (0: one wave, wave_tiles)
+  int64_t own_tiles = 0;
   std::string err;
 };
 
@@ -235,6 +238,21 @@ cudaError_t rebuild(ka_batch* b) {
   for (auto& gc : b->graph) b->units += (int64_t)gc.units.size();
   b->idle_units = 0;
   return cudaStreamSynchronize(b->stream);
+}
+
+// Whether a job shares the batched launches: graphs always; a cubic lattice
+// on the pencil kernels unless its groups have own_tiles tiles or more (it
+// then runs with its own launches inside each round: the group kernels of
+// three-dimensional lattices or the single-instance pencil kernel, arguments
+// in the constant bank); a cubic lattice on the edge-gather path never.
+bool shares_launches(const ka_batch* b, const ka_ctx* ctx) {
+  if (ctx->topo != KA_CUBIC) return true;
+  if (!ctx->pencil) return false;
+  int64_t pencils = 1;
+  for (int k = 0; k < ctx->d - 1; ++k) pencils *= ctx->L;
+  if (ctx->d >= 2) pencils /= 2;
+  const int64_t tiles = (pencils + ka::kCubicWarps / ctx->pl.V - 1) / (ka::kCubicWarps / ctx->pl.V);
+  return tiles < (b->own_tiles > 0 ? b->own_tiles : b->wave_tiles);
 }
 
 // sweeps job j may run in a round of length k: up to its next observation or its target
@@ -426,19 +444,8 @@ ka_status enrol(ka_batch* b, ka_ctx* ctx, const ka_job_spec* spec, int64_t* job_
   j->target = spec->sweeps;
   j->every = spec->observe_every;
   j->cap = spec->sweeps / spec->observe_every + 2;
-  // Small jobs share the batched launches.  A cubic lattice whose groups have
-  // a full wave of tiles on their own runs with its own launches (the
-  // single-instance kernel, arguments in the constant bank) -- as does a
-  // cubic lattice on the edge-gather path.
-  if (ctx->topo == KA_CUBIC) {
-    int64_t pencils = 1;
-    for (int k = 0; k < ctx->d - 1; ++k) pencils *= ctx->L;
-    if (ctx->d >= 2) pencils /= 2;
-    const int64_t tiles = (pencils + ka::kCubicWarps / ctx->pl.V - 1) / (ka::kCubicWarps / ctx->pl.V);
-    j->batched = ctx->pencil && tiles < b->wave_tiles;
-  } else {
-    j->batched = true;
-  }
+  // small jobs share the batched launches (shares_launches)
+  j->batched = shares_launches(b, ctx);
   const ka_status st = observe_job(b, j);
   if (st) {
     cudaFree(j->obs_dev);
@@ -453,6 +460,58 @@ ka_status enrol(ka_batch* b, ka_ctx* ctx, const ka_job_spec* spec, int64_t* job_
   b->dirty = true;
   if (job_id) *job_id = j->id;
   return KA_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Site-word-sweeps one round of length k would run (the unfinished jobs).
+double round_work(const ka_batch* b, int64_t k) {
+  double work = 0.0;
+  for (auto& kv : b->jobs) {
+    const Job* j = kv.second;
+    if (!j->finished) work += (double)j->ctx->N * (j->ctx->R / 64) * (double)allowance(j, k);
+  }
+  return work;
+}
+
+// Site-word-sweeps per ms of rounds of length k in the batch's present
+// configuration: warm-up rounds first (the first builds the tables; in graph
+// mode the second captures the round, a length being captured on its second
+// use), then one timed round.  All rounds do real work.  Returns < 0 when no
+// job is left to run.
+double time_rounds(ka_batch* b, int64_t k, cudaEvent_t e0, cudaEvent_t e1, ka_status* st) {
+  int64_t ran = 0;
+  const int warm = (b->flags & KA_BATCH_GRAPH) ? 2 : 1;
+  for (int w = 0; w < warm && !*st; ++w) *st = run_round(b, k, &ran);
+  if (*st || ran == 0) return -1.0;
+  const double work = round_work(b, k);
+  if (work == 0.0) return -1.0;
+  cudaEventRecord(e0, b->stream);
+  *st = run_round(b, k, &ran);
+  cudaEventRecord(e1, b->stream);
+  cudaEventSynchronize(e1);
+  if (*st) return -1.0;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  return work / (ms > 0.f ? ms : 1e-3f);
+}
+
+// Put every unfinished cubic job on its own or the shared launches for the
+// threshold own_tiles; the tables are rebuilt before the next round if any
+// job moved.
+void apply_own_tiles(ka_batch* b, int64_t own_tiles) {
+  b->own_tiles = own_tiles;
+  for (auto& kv : b->jobs) {
+    Job* j = kv.second;
+    if (j->finished) continue;
+    const bool shared = shares_launches(b, j->ctx);
+    if (shared != j->batched) {
+      j->batched = shared;
+      b->dirty = true;
+    }
+  }
 }
 
 }  // namespace
@@ -558,36 +617,37 @@ ka_status ka_batch_autotune(ka_batch* b, int64_t* best_round) {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(b->device);
-  const int64_t cand[] = {4, 16, 64};
-  double best = -1.0;
-  int64_t best_k = b->tuned_k;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   ka_status st = KA_OK;
-  for (int64_t k : cand) {
-    // warm-up rounds of length k: the first builds the tables, and in graph
-    // mode the second captures the round (a length is captured on its second
-    // use); the next round is timed as the steady state
-    int64_t ran = 0;
-    const int warm = (b->flags & KA_BATCH_GRAPH) ? 2 : 1;
-    for (int w = 0; w < warm && !st; ++w) st = run_round(b, k, &ran);
-    if (st || ran == 0) break;
-    // work of the timed round: site-words times sweeps over the unfinished jobs
-    double work = 0.0;
-    for (auto& kv : b->jobs) {
-      const Job* j = kv.second;
-      if (!j->finished) work += (double)j->ctx->N * (j->ctx->R / 64) * (double)allowance(j, k);
+  // (1) which cubic jobs run with their own launches: the tile threshold, at
+  // the present round length (one wave of tiles, half, a quarter, an eighth,
+  // or no job on its own launches)
+  if (!(b->flags & KA_BATCH_PLAIN)) {
+    const int64_t w = b->wave_tiles;
+    const int64_t cand[] = {w, w / 2, w / 4, w / 8, INT64_MAX};
+    double best = -1.0;
+    int64_t best_t = b->own_tiles > 0 ? b->own_tiles : w;
+    for (int64_t t : cand) {
+      apply_own_tiles(b, t);
+      const double rate = time_rounds(b, b->tuned_k, e0, e1, &st);
+      if (st || rate < 0.0) break;
+      if (rate > best) {
+        best = rate;
+        best_t = t;
+      }
     }
-    if (work == 0.0) break;
-    cudaEventRecord(e0, b->stream);
-    st = run_round(b, k, &ran);
-    cudaEventRecord(e1, b->stream);
-    cudaEventSynchronize(e1);
+    if (!st) apply_own_tiles(b, best_t);
+  }
+  // (2) the round length, with that threshold
+  const int64_t cand_k[] = {4, 16, 64};
+  double best = -1.0;
+  int64_t best_k = b->tuned_k;
+  for (int64_t k : cand_k) {
     if (st) break;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    const double rate = work / (ms > 0.f ? ms : 1e-3f);
+    const double rate = time_rounds(b, k, e0, e1, &st);
+    if (st || rate < 0.0) break;
     if (rate > best) {
       best = rate;
       best_k = k;
@@ -599,6 +659,13 @@ ka_status ka_batch_autotune(ka_batch* b, int64_t* best_round) {
   if (best_round) *best_round = best_k;
   if (prev >= 0) cudaSetDevice(prev);
   return st;
+}
+
+ka_status ka_batch_tuning(const ka_batch* b, int64_t* round_sweeps, int64_t* own_tiles) {
+  if (!b) return KA_EINVAL;
+  if (round_sweeps) *round_sweeps = b->tuned_k;
+  if (own_tiles) *own_tiles = b->own_tiles > 0 ? b->own_tiles : b->wave_tiles;
+  return KA_OK;
 }
 
 ka_status ka_batch_poll(const ka_batch* b, int64_t job_id, int64_t* sweep, int32_t* finished) {

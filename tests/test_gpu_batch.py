@@ -139,12 +139,29 @@ def test_budget_admission_and_release():
 
 def test_autotune_picks_a_candidate():
     with K.Batch() as b:
+        k0, t0 = b.tuning()
+        assert k0 == 16 and t0 > 0  # before tuning: one wave of tiles
         for j in JOBS[:6]:
             b.add(200, 100, j["seed"], j["rho"], **j["params"])
         k = b.autotune()
         assert k in (4, 16, 64)
+        kt, t = b.tuning()
+        assert kt == k and t in (t0, t0 // 2, t0 // 4, t0 // 8, 2 ** 63 - 1)
         while b.info()["active"]:
             b.step()
+
+
+def test_autotuned_mix_matches_the_oracle(oracle_results):
+    # tuning moves cubic jobs between their own and the shared launches
+    # mid-run; every job still ends with the oracle's observations and planes
+    with K.Batch() as b:
+        ids = [b.add(j["sweeps"], j["every"], j["seed"], j["rho"], **j["params"]) for j in JOBS]
+        b.step(2)
+        b.autotune()
+        while b.info()["active"]:
+            b.step()
+        for jid, job, want in zip(ids, JOBS, oracle_results):
+            _check_job(b, jid, job, want)
 
 
 def test_adopt_rules():
