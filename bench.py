@@ -18,6 +18,8 @@ which also carries (one GPU):
   rho = 0.55 .. 0.90, with its own roofline at 48 bytes per site-word-sweep;
 * ``batched``: a bounded sample of the 512-instance mix run batched and with
   per-job launches on the same GPU (``batched_over_plain``);
+* ``served``: a bounded sample of the request trace through the serving loop
+  (moves/s, p50/p99 latency at 200 requests/s and at 0.7 of the capacity);
 * ``cpu_baseline``: the CPU oracle on one core and on every host core
   (processes over replica blocks), with the core count and CPU model.
 
@@ -429,6 +431,39 @@ def native_line(*, world, steps, warmup, sweeps, ms, value, achieved, peak, peak
     return line
 
 
+def run_served_sample(jobs_n: int, scale: float, round_sweeps: int = 0) -> dict:
+    """A bounded sample of the request trace through the serving loop: the
+    first jobs_n requests at 200/s, then the same requests at 0.7 of the
+    capacity (jobs/s) the first run measured."""
+    import paper_1710_05155_gb300.serve as Sv
+    from paper_1710_05155_gb300 import workloads
+
+    budget = int(150 * (1 << 30))
+
+    def serve(rate):
+        jobs = workloads.scaled(workloads.request_trace(jobs_n, rate, 1), scale)
+        be = Sv.DeviceBackend(0, budget, True, 4)
+        try:
+            rep = Sv.Server(be, round_sweeps=round_sweeps).run(jobs)
+        finally:
+            be.close()
+        rep["rate_per_s"] = rate
+        rep["mean_job_moves"] = float(np.mean([j.work for j in jobs]))
+        return rep
+
+    first = serve(200.0)
+    capacity = first["moves_per_s"] / first["mean_job_moves"]
+    second = serve(0.7 * capacity)
+    keep = ("moves_per_s", "latency_p50_s", "latency_p99_s", "queue_p50_s", "service_p50_s",
+            "makespan_s", "done", "max_running", "rate_per_s")
+    return {"value": first["moves_per_s"], "unit": UNIT,
+            "workload": f"the first {jobs_n} requests of the Poisson trace (200/s; cubic L in "
+                        f"4*[8..32] or RRG z=4 N=2^14..2^20, m in {{2,3}}, R in {{64..256}}), "
+                        f"sweeps x {scale}, 150 GB budget",
+            "offered_200_per_s": {k: first[k] for k in keep},
+            "at_0.7_capacity": {"capacity_jobs_per_s": capacity, **{k: second[k] for k in keep}}}
+
+
 def run_native(args, rank: int, world: int) -> None:
     import torch
 
@@ -569,6 +604,8 @@ def run_native(args, rank: int, world: int) -> None:
                 extra["rrg"] = run_rrg(dev, stream, args.rrg_sweeps)
             if not args.no_batched:
                 extra["batched"] = run_batched_sample(dev, args.batched_jobs, args.batched_scale)
+            if not args.no_served:
+                extra["served"] = run_served_sample(args.served_jobs, args.batched_scale)
             if not args.no_cpu_baseline:
                 extra["cpu_baseline"] = cpu_baseline()
         line = native_line(
@@ -701,6 +738,9 @@ def main():
                     help="reference arm: oracle processes (0: every host core)")
     ap.add_argument("--no-rrg", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-jobs", type=int, default=40,
+                    help="served sample of the main line: requests of the trace")
     ap.add_argument("--rrg-sweeps", type=int, default=100, help="rrg: sweeps per density")
     ap.add_argument("--batched-jobs", type=int, default=128,
                     help="batched sample of the main line: instances of the mix")
