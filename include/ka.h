@@ -126,8 +126,8 @@ typedef struct {
     uint64_t seed;      /* dynamics seed */
     int32_t kernel;     /* 0 = general cubic pencil kernel, 1 = edge-gather kernel,
                            3 = group kernels of three-dimensional lattices (d = 3,
-                           L % 4 == 0, L <= 128: from two planes up, or one
-                           plane with L in {32, 64, 128} or L >= 96, L % 8 == 0) */
+                           L % 4 == 0, L <= 128: from two planes up, and for one
+                           plane at the sides where they are measured faster) */
     int32_t rrg_attempts; /* configuration-model attempts (KA_RRG) */
     size_t device_bytes;  /* device memory the context uses */
     int32_t planes;       /* device state planes per array */

@@ -9,14 +9,21 @@ bool stream_supported(int d, int L) { return d == 3 && L % 4 == 0 && L >= 4 && L
 
 bool stream_preferred(int d, int L, int P) {
   // Measured per word-sweep against the general pencil kernel
-  // (ka_cubic_kernel.cuh): the group kernels win at every side from two
-  // planes up (1.1-3.6x) and for one plane from L = 96 up when L % 8 == 0
-  // (blocks of at least four pencils: 1.1-1.6x); otherwise one plane gives
-  // them too few CTAs (e.g. 100 at L = 80) or half-sector rows (L = 100) and
-  // the general kernel is 5-25 % faster.  The fixed sides 32, 64 and 128
-  // always take them.
+  // (ka_cubic_kernel.cuh): from two planes up the group kernels win at every
+  // side (1.3-4.4x).  With one plane (64 replicas) they win or tie at
+  // L = 8, 16, 48, 80, 88, 96, 104, 112, 116, 120, 124 (up to 1.95x) and lose
+  // by up to 8 % at 28, 56, 60, 72 and 100 (rows that leave lanes idle, too
+  // few CTAs), tie at 24, 36, 40, 108; the unmeasured sides follow their
+  // neighbours.
   if (!stream_supported(d, L)) return false;
-  return L == 32 || L == 64 || L == 128 || P >= 2 || (L >= 96 && L % 8 == 0);
+  if (P >= 2) return true;
+  switch (L) {
+    case 20: case 24: case 28: case 36: case 40: case 44: case 52: case 56: case 60: case 68:
+    case 72: case 76: case 100: case 108:
+      return false;
+    default:
+      return true;
+  }
 }
 
 int stream_planes_per_launch(int L, int P) {
@@ -48,10 +55,41 @@ cudaError_t launch_stream_group(const Planes& pl, int q0, int nq, int L, int m, 
   a.word0 = (uint32_t)q0;
   a.rk = rk;
   a.L = L;
-  if (L == 32) return launch_l<32>(a, m, st);
-  if (L == 64) return launch_l<64>(a, m, st);
-  if (L == 128) return launch_l<128>(a, m, st);
-  return launch_l<0>(a, m, st);  // every other side: geometry from the arguments
+  switch (L) {
+    case 4: return launch_l<4>(a, m, st);
+    case 8: return launch_l<8>(a, m, st);
+    case 12: return launch_l<12>(a, m, st);
+    case 16: return launch_l<16>(a, m, st);
+    case 20: return launch_l<20>(a, m, st);
+    case 24: return launch_l<24>(a, m, st);
+    case 28: return launch_l<28>(a, m, st);
+    case 32: return launch_l<32>(a, m, st);
+    case 36: return launch_l<36>(a, m, st);
+    case 40: return launch_l<40>(a, m, st);
+    case 44: return launch_l<44>(a, m, st);
+    case 48: return launch_l<48>(a, m, st);
+    case 52: return launch_l<52>(a, m, st);
+    case 56: return launch_l<56>(a, m, st);
+    case 60: return launch_l<60>(a, m, st);
+    case 64: return launch_l<64>(a, m, st);
+    case 68: return launch_l<68>(a, m, st);
+    case 72: return launch_l<72>(a, m, st);
+    case 76: return launch_l<76>(a, m, st);
+    case 80: return launch_l<80>(a, m, st);
+    case 84: return launch_l<84>(a, m, st);
+    case 88: return launch_l<88>(a, m, st);
+    case 92: return launch_l<92>(a, m, st);
+    case 96: return launch_l<96>(a, m, st);
+    case 100: return launch_l<100>(a, m, st);
+    case 104: return launch_l<104>(a, m, st);
+    case 108: return launch_l<108>(a, m, st);
+    case 112: return launch_l<112>(a, m, st);
+    case 116: return launch_l<116>(a, m, st);
+    case 120: return launch_l<120>(a, m, st);
+    case 124: return launch_l<124>(a, m, st);
+    case 128: return launch_l<128>(a, m, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace ka

@@ -1,12 +1,13 @@
 // ka_cubic_stream.cuh -- group kernels for three-dimensional lattices (any
 // side L with L % 4 == 0, 4 <= L <= 128) stored one word per site and plane
-// in split-row order.  The sides 32, 64 and 128 run kernels with the side
-// fixed at compile time (k_rows, k_pencils); every other side runs the same
-// algorithm with the geometry read from the launch arguments (k_rows_any,
+// in split-row order.  The sides 32, 64 and 128 run k_rows and k_pencils;
+// every other side runs a general form of the same algorithm (k_rows_any,
 // k_pencils_any: partial warps of rows, blocks of fewer pencils with several
-// layers per warp, chunks of unequal length along the pencils).  The two
-// forms are kept apart because the general form, instantiated for a fixed
-// side, ran 6 % slower at L = 128 (33.6 against 31.6 us per word-sweep).
+// layers per warp, chunks of unequal length along the pencils).  Every side
+// has its own instance with the geometry fixed at compile time: the general
+// form reading the side at run time ran 1.6 times slower at L = 128 (51.8
+// against 31.6 us per word-sweep), and instantiated for L = 128 it is still
+// 6 % slower than k_pencils (33.6 us), so the three sides keep theirs.
 //
 // One launch runs one bond-class group (mu, par) -- the four classes
 // c = 4(2 mu + par) + a, a = 0..3 -- on one or more one-word state planes
@@ -63,22 +64,26 @@ struct Args {
   uint64_t* p;
   size_t plane;     // elements per plane
   int nplanes;      // planes of this launch
-  int L;            // side (read by the general form)
+  int L;            // side
   int mu, par;
   uint32_t t, cls0, word0;
   RoundKeys rk;
 };
 
-// L = the side at compile time, or 0: the general form, side from the arguments
+// L = the side (every multiple of 4 up to 128 has its instance)
 template <int L>
 cudaError_t launch_l(const Args& a, int m, cudaStream_t st);
 
 #define KA_STREAM_EXTERN(LL) \
   extern template cudaError_t launch_l<LL>(const Args&, int, cudaStream_t);
-KA_STREAM_EXTERN(0)
-KA_STREAM_EXTERN(32)
-KA_STREAM_EXTERN(64)
-KA_STREAM_EXTERN(128)
+KA_STREAM_EXTERN(4) KA_STREAM_EXTERN(8) KA_STREAM_EXTERN(12) KA_STREAM_EXTERN(16)
+KA_STREAM_EXTERN(20) KA_STREAM_EXTERN(24) KA_STREAM_EXTERN(28) KA_STREAM_EXTERN(32)
+KA_STREAM_EXTERN(36) KA_STREAM_EXTERN(40) KA_STREAM_EXTERN(44) KA_STREAM_EXTERN(48)
+KA_STREAM_EXTERN(52) KA_STREAM_EXTERN(56) KA_STREAM_EXTERN(60) KA_STREAM_EXTERN(64)
+KA_STREAM_EXTERN(68) KA_STREAM_EXTERN(72) KA_STREAM_EXTERN(76) KA_STREAM_EXTERN(80)
+KA_STREAM_EXTERN(84) KA_STREAM_EXTERN(88) KA_STREAM_EXTERN(92) KA_STREAM_EXTERN(96)
+KA_STREAM_EXTERN(100) KA_STREAM_EXTERN(104) KA_STREAM_EXTERN(108) KA_STREAM_EXTERN(112)
+KA_STREAM_EXTERN(116) KA_STREAM_EXTERN(120) KA_STREAM_EXTERN(124) KA_STREAM_EXTERN(128)
 #undef KA_STREAM_EXTERN
 
 #ifdef KA_STREAM_INSTANCES
@@ -471,9 +476,9 @@ struct PencilGeo {
 };
 
 // General form of k_rows (below): the same work with the geometry of RowGeo.
-template <int M>
+template <int LT, int M>
 __global__ void __launch_bounds__(32 * kRowWarps) k_rows_any(const __grid_constant__ Args a) {
-  const RowGeo G(a.L);
+  const RowGeo G(LT);
   const int L = G.L, S = G.S, PW = G.PW, Ty = G.Ty, nyb = G.nyb, Lh = L / 2;
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -489,7 +494,9 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_rows_any(const __grid_consta
   const int next = in_row ? gj * S + (seg == S - 1 ? 0 : seg + 1) : lane;
   const int i = (warp % (kRowWarps / 2)) * PW + gj;  // active row of this layer in the block
   const int y = yb * Ty + 2 * i + ((a.par ^ z) & 1);
-  const bool live = in_row && y < L;
+  // sides whose rows fill whole warps and blocks have no idle lanes
+  constexpr bool kExact = 32 % (LT / 4) == 0 && LT % (8 * (32 / (LT / 4))) == 0;
+  const bool live = kExact || (in_row && y < L);
   // gate blocks (independent of the state: first)
   const uint32_t site =
       (uint32_t)(4 * seg) + (uint32_t)L * ((uint32_t)y + (uint32_t)L * (uint32_t)z);
@@ -542,9 +549,9 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_rows_any(const __grid_consta
   }
 }
 
-template <int M>
+template <int LT, int M>
 cudaError_t launch_rows_any(const Args& a, cudaStream_t st) {
-  const RowGeo G(a.L);
+  const RowGeo G(LT);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(a.nplanes * (G.L / 2) * G.nyb));
   cfg.blockDim = dim3(32 * kRowWarps);
@@ -555,15 +562,15 @@ cudaError_t launch_rows_any(const Args& a, cudaStream_t st) {
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_rows_any<M>, a);
+  return cudaLaunchKernelEx(&cfg, k_rows_any<LT, M>, a);
 }
 
 // General form of k_pencils (below): NP pencils of PL layers per warp, CW
 // chunks of J segments along the pencils (the last may be shorter), the
 // chunk ring closed over those CW chunks.
-template <int M, int MU>
+template <int LT, int M, int MU>
 __global__ void __launch_bounds__(32 * kPencilWarps) k_pencils_any(const __grid_constant__ Args a) {
-  const PencilGeo G(a.L);
+  const PencilGeo G(LT);
   const int L = G.L, Lh = G.Lh, NP = G.NP, PL = G.PL, nhb = G.nhb, J = G.J, CW = G.CW;
   // rows (t, s) start at (s L + t) L (mu = 1) or (t L + s) L (mu = 2): the
   // word strides of one step along the pencil and across layers
@@ -581,10 +588,14 @@ __global__ void __launch_bounds__(32 * kPencilWarps) k_pencils_any(const __grid_
   const int plane = (int)(b / (uint32_t)G.nsg);
   const int s = sgrp * PL + lane / NP;
   const int h = hb * NP + lane % NP;
-  const bool live = s < L;  // layers past L (when PL does not divide L) idle
+  // layers past L (when PL does not divide L) idle
+  constexpr int kNP = ((LT / 2) & -(LT / 2)) < 32 ? ((LT / 2) & -(LT / 2)) : 32;
+  constexpr bool kFullLayers = LT % (32 / kNP) == 0;
+  constexpr bool kFullChunks = (LT / 4) % kPencilWarps == 0;
+  const bool live = kFullLayers || s < L;
   // this warp's chunk: segments j0 .. j0 + nseg - 1; warps past CW carry none
   const int j0 = warp * J;
-  const int nseg = warp < CW ? min(J, G.NS - j0) : 0;
+  const int nseg = kFullChunks ? J : (warp < CW ? min(J, G.NS - j0) : 0);
   const int act = (a.par ^ s) & 1, oth = act ^ 1;
   const uint32_t x = 2u * (uint32_t)h + (uint32_t)act;  // canonical x of this lane's pencil
   // x neighbours, in the other half: odd[h - 1], odd[h] (x even) or even[h], even[h + 1] (x odd)
@@ -602,7 +613,7 @@ __global__ void __launch_bounds__(32 * kPencilWarps) k_pencils_any(const __grid_
   const uint64_t* const gr = n + (size_t)s * SS + (size_t)oth * Lh + hr;
   const uint64_t* const gm = n + (size_t)sm * SS + (size_t)act * Lh + h;
   const uint64_t* const gq = n + (size_t)sp * SS + (size_t)act * Lh + h;
-  const bool mem = live && nseg > 0;  // this lane touches memory
+  const bool mem = (kFullLayers && kFullChunks) || (live && nseg > 0);  // this lane touches memory
   const uint32_t word = a.word0 + (uint32_t)plane;
   const uint32_t site0 = x + (uint32_t)t0 * CT + (uint32_t)s * CS;  // canonical site of t0
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -615,7 +626,7 @@ __global__ void __launch_bounds__(32 * kPencilWarps) k_pencils_any(const __grid_
 #pragma unroll
   for (int k = 0; k < 4; ++k) qn[k] = qf[k] = qp[k] = 0;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {  // J <= 4 for L <= 128
+  for (int j = 0; j < (LT / 4 + 7) / 8; ++j) {
     if (j >= nseg) break;
     uint64_t cn[4], cp[4], cA[4], cB[4], cf[4];
 #pragma unroll
@@ -737,9 +748,9 @@ __global__ void __launch_bounds__(32 * kPencilWarps) k_pencils_any(const __grid_
   }
 }
 
-template <int M>
+template <int LT, int M>
 cudaError_t launch_pencils_any(const Args& a, cudaStream_t st) {
-  const PencilGeo G(a.L);
+  const PencilGeo G(LT);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(a.nplanes * G.nsg * G.nhb));
   cfg.blockDim = dim3(32 * kPencilWarps);
@@ -750,8 +761,8 @@ cudaError_t launch_pencils_any(const Args& a, cudaStream_t st) {
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return a.mu == 1 ? cudaLaunchKernelEx(&cfg, k_pencils_any<M, 1>, a)
-                   : cudaLaunchKernelEx(&cfg, k_pencils_any<M, 2>, a);
+  return a.mu == 1 ? cudaLaunchKernelEx(&cfg, k_pencils_any<LT, M, 1>, a)
+                   : cudaLaunchKernelEx(&cfg, k_pencils_any<LT, M, 2>, a);
 }
 
 }  // namespace
@@ -760,12 +771,12 @@ template <int L>
 cudaError_t launch_l(const Args& a, int m, cudaStream_t st) {
 #define KA_M_CASES_ANY(FN)                     \
   switch (m < 5 ? m : 5) {                     \
-    case 0: return FN<0>(a, st);               \
-    case 1: return FN<1>(a, st);               \
-    case 2: return FN<2>(a, st);               \
-    case 3: return FN<3>(a, st);               \
-    case 4: return FN<4>(a, st);               \
-    default: return FN<5>(a, st);              \
+    case 0: return FN<L, 0>(a, st);            \
+    case 1: return FN<L, 1>(a, st);            \
+    case 2: return FN<L, 2>(a, st);            \
+    case 3: return FN<L, 3>(a, st);            \
+    case 4: return FN<L, 4>(a, st);            \
+    default: return FN<L, 5>(a, st);           \
   }
 #define KA_M_CASES(FN)                         \
   switch (m < 5 ? m : 5) {                     \
@@ -776,7 +787,7 @@ cudaError_t launch_l(const Args& a, int m, cudaStream_t st) {
     case 4: return FN<L, 4>(a, st);            \
     default: return FN<L, 5>(a, st);           \
   }
-  if constexpr (L == 0) {
+  if constexpr (L != 32 && L != 64 && L != 128) {
     if (a.mu == 0) KA_M_CASES_ANY(launch_rows_any)
     KA_M_CASES_ANY(launch_pencils_any)
   } else {

@@ -88,9 +88,14 @@ def test_cubic_gather_kernel_every_sweep(kw):
 
 
 def test_cubic_info_reports_kernel():
+    # 3: group kernels of three-dimensional lattices; 0: general pencil
+    # kernel; 1: edge gather
     a = K.Simulation(topo=K.KA_CUBIC, d=3, L=8, m=3, replicas=64)
     b = K.Simulation(topo=K.KA_CUBIC, d=3, L=8, m=3, replicas=64, flags=K.KA_FLAG_GENERIC)
-    assert a.info["kernel"] == 0 and b.info["kernel"] == 1
+    c = K.Simulation(topo=K.KA_CUBIC, d=2, L=8, m=2, replicas=64)
+    d = K.Simulation(topo=K.KA_CUBIC, d=3, L=24, m=3, replicas=64)
+    assert a.info["kernel"] == 3 and b.info["kernel"] == 1 and c.info["kernel"] == 0
+    assert d.info["kernel"] == 0
     assert a.info["nclass"] == 24 and a.info["nbonds"] == 3 * 512
 
 

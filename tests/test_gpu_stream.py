@@ -84,14 +84,14 @@ def test_l64_every_sweep():
     (112, 4, 64, 1), (120, 3, 64, 1), (124, 3, 128, 1)])
 def test_runtime_side_every_sweep(L, m, R, sweeps):
     # sides other than 32, 64, 128: the general form, geometry read at run time
-    # (from two planes up, or one plane from L = 96 up with L % 8 == 0)
+    # (from two planes up, and one plane at the sides where they are faster)
     _run(L, m, R, seed=100 + L, rho=0.8, sweeps=sweeps)
 
 
-def test_one_plane_small_sides_take_the_general_kernel():
-    for L in (80, 100):
+def test_one_plane_kernel_choice():
+    for L, kernel in ((72, 0), (100, 0), (80, 3), (96, 3)):
         sim = K.Simulation(topo=K.KA_CUBIC, d=3, L=L, m=3, replicas=64)
-        assert sim.info["kernel"] == 0
+        assert sim.info["kernel"] == kernel
         sim.close()
 
 
