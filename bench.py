@@ -21,7 +21,11 @@ which also carries (one GPU):
 * ``served``: a bounded sample of the request trace through the serving loop
   (moves/s, p50/p99 latency at 200 requests/s and at 0.7 of the capacity);
 * ``cpu_baseline``: the CPU oracle on one core and on every host core
-  (processes over replica blocks), with the core count and CPU model.
+  (processes over replica blocks), with the core count and CPU model;
+* ``small``: the small configuration (d=3, L=16, m=3, 64 replicas, 1000
+  sweeps observed every 10) in full on the GPU, and the oracle on 8 host
+  processes for the same whole run; the ``rrg`` key carries the oracle on the
+  random regular graph as its own ``cpu_baseline``.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--sweeps S] [--impl native|reference]
 
@@ -174,36 +178,48 @@ def cpu_model() -> str:
     return platform.processor() or platform.machine()
 
 
-def _oracle_worker(conn, r0: int, n_rep: int, rho: float) -> None:
-    """One oracle process: replicas r0 .. r0 + n_rep - 1 of the cubic workload;
-    answers every "sweep k" message with the seconds its k sweeps took."""
+# the workloads the oracle is timed on: (topology, parameters, m)
+ORACLE_CUBIC = ("cubic", (D, L), M)
+ORACLE_SMALL = ("cubic", (3, 16), 3)                         # d=3 L=16 m=3 (the small config)
+ORACLE_RRG = ("rrg", (RRG_N, RRG_Z, RRG_GRAPH_SEED), RRG_M)  # N=2^20 z=4 m=2
+
+
+def _oracle_worker(conn, r0: int, n_rep: int, rho: float, spec=ORACLE_CUBIC) -> None:
+    """One oracle process: replicas r0 .. r0 + n_rep - 1 of a workload; answers
+    every (k, observe) message with the seconds its k sweeps (and, if asked,
+    one observation) took."""
     import oracle as O
 
-    topo = O.cubic(D, L)
+    kind, prm, m = spec
+    topo = O.cubic(*prm) if kind == "cubic" else O.rrg(*prm)
     st = O.init(topo.N, n_rep, SEED, rho, r0=r0)
     conn.send("ready")
     while True:
-        k = conn.recv()
-        if k is None:
+        msg = conn.recv()
+        if msg is None:
             break
+        k, obs = msg
         t0 = time.perf_counter()
-        O.sweeps(topo, M, st, SEED, k)
+        O.sweeps(topo, m, st, SEED, k)
+        if obs:
+            O.observe(st)
         conn.send(time.perf_counter() - t0)
     conn.close()
 
 
 class OracleBlocks:
     """The CPU oracle over `workers` processes (spawned), each holding its own
-    block of replicas of the cubic workload: replicas are independent, so the
-    blocks sweep in parallel.  step(k) runs k sweeps on every block and
-    returns the wall time until the last block is done."""
+    block of replicas of a workload: replicas are independent, so the blocks
+    sweep in parallel.  step(k) runs k sweeps on every block and returns the
+    wall time until the last block is done."""
 
-    def __init__(self, workers: int, n_rep: int, rho: float = RHOS[0]):
+    def __init__(self, workers: int, n_rep: int, rho: float = RHOS[0], spec=ORACLE_CUBIC):
         ctx = mp.get_context("spawn")
         self.conns, self.procs = [], []
         for w in range(workers):
             a, b = ctx.Pipe()
-            p = ctx.Process(target=_oracle_worker, args=(b, w * n_rep, n_rep, rho), daemon=True)
+            p = ctx.Process(target=_oracle_worker, args=(b, w * n_rep, n_rep, rho, spec),
+                            daemon=True)
             p.start()
             self.conns.append(a)
             self.procs.append(p)
@@ -211,10 +227,10 @@ class OracleBlocks:
             assert c.recv() == "ready"
         self.workers, self.n_rep = workers, n_rep
 
-    def step(self, k: int) -> float:
+    def step(self, k: int, observe: bool = False) -> float:
         t0 = time.perf_counter()
         for c in self.conns:
-            c.send(k)
+            c.send((k, observe))
         for c in self.conns:
             c.recv()
         return time.perf_counter() - t0
@@ -364,6 +380,65 @@ def run_rrg(dev: int, stream, sweeps: int) -> dict:
                      "avg_launch_us_isolated": 1000.0 * float(iso_ms.sum() / max(iso_n.sum(), 1))},
         "gpu_launches": launches,
     }
+
+
+def rrg_oracle_baseline(n_rep: int = 8, sweeps: int = 2) -> dict:
+    """The oracle on every host core for the random regular graph workload
+    (N=2^20, z=4, m=2, rho=0.55): n_rep replicas per process, `sweeps` sweeps."""
+    cores = host_cores()
+    blocks = OracleBlocks(min(cores, 8), n_rep, RRG_RHOS[0], ORACLE_RRG)  # 64 replicas at most
+    dt = blocks.step(sweeps)
+    blocks.close()
+    nrep = n_rep * blocks.workers
+    return {"value": RRG_N * nrep * sweeps / dt, "unit": UNIT, "kind": "oracle",
+            "cores": blocks.workers, "cpu_model": cpu_model(),
+            "sample": f"RRG N=2^20 z=4 m=2 rho=0.55, {nrep} of 64 replicas ({n_rep} per process), "
+                      f"{sweeps} sweeps after an untimed initial state"}
+
+
+def run_small(dev: int, stream, oracle: bool) -> dict:
+    """The small configuration in full: d=3, L=16, m=3, rho=0.70, 64 replicas,
+    1000 sweeps observed every 10 sweeps (101 observations), seed 1 -- on the
+    GPU (counts into device memory, one context) and, when asked, the oracle
+    on 8 host processes of 8 replicas each, the same sweeps and observations."""
+    import torch
+
+    import paper_1710_05155_gb300 as K
+
+    Ls, sweeps, every, rho = 16, 1000, 10, 0.70
+    sim = K.Simulation(topo=K.KA_CUBIC, d=3, L=Ls, m=3, replicas=64, device=dev, stream=stream)
+    counts = torch.zeros((sweeps // every + 1, 64, 4), dtype=torch.int64, device=f"cuda:{dev}")
+    runs = []
+    for _ in range(3):  # the first run warms up
+        sim.init(SEED, rho)
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        K.ka_observe_device(sim.ctx, counts[0].data_ptr())
+        for k in range(1, sweeps // every + 1):
+            K.ka_sweep(sim.ctx, every)
+            K.ka_observe_device(sim.ctx, counts[k].data_ptr())
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        runs.append(ev0.elapsed_time(ev1))
+    kernel = sim.info["kernel"]
+    sim.close()
+    ms = min(runs[1:])
+    moves = Ls ** 3 * 64 * sweeps
+    out = {"value": moves / (ms / 1000.0), "unit": UNIT, "ms": ms, "kernel": kernel,
+           "workload": "cubic d=3 L=16 z=6 m=3, rho=0.70, 64 replicas, 1000 sweeps, "
+                       "observed every 10 sweeps, seed 1"}
+    if oracle:
+        blocks = OracleBlocks(8, 8, rho, ORACLE_SMALL)
+        dt = blocks.step(0, True)
+        for _ in range(sweeps // every):
+            dt += blocks.step(every, True)
+        blocks.close()
+        out["cpu_baseline"] = {"value": moves / dt, "unit": UNIT, "kind": "oracle", "cores": 8,
+                               "cpu_model": cpu_model(), "seconds": dt,
+                               "sample": "the whole run: 64 replicas in 8 processes of 8, "
+                                         "1000 sweeps and 101 observations"}
+    return out
 
 
 def run_batched_sample(dev: int, jobs_n: int, scale: float) -> dict:
@@ -602,6 +677,10 @@ def run_native(args, rank: int, world: int) -> None:
         if world == 1:
             if not args.no_rrg:
                 extra["rrg"] = run_rrg(dev, stream, args.rrg_sweeps)
+                if not args.no_cpu_baseline:
+                    extra["rrg"]["cpu_baseline"] = rrg_oracle_baseline()
+            if not args.no_small:
+                extra["small"] = run_small(dev, stream, not args.no_cpu_baseline)
             if not args.no_batched:
                 extra["batched"] = run_batched_sample(dev, args.batched_jobs, args.batched_scale)
             if not args.no_served:
@@ -739,6 +818,7 @@ def main():
     ap.add_argument("--no-rrg", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--served-jobs", type=int, default=40,
                     help="served sample of the main line: requests of the trace")
     ap.add_argument("--rrg-sweeps", type=int, default=100, help="rrg: sweeps per density")
