@@ -3,10 +3,11 @@
 // Every job is an ordinary context (own device buffer, topology, seed,
 // density, replica count) plus a device buffer of observations.  A round
 // advances all unfinished jobs by up to k sweeps: for every sweep offset s
-// and every bond-class group, ONE launch of the pencil kernel covers all
-// cubic work units (job planes) of a shape class (d, V, m), and ONE launch of
-// the edge-gather kernel covers class c of all graph units of a shape class
-// (V, m).  Units carry their own sweep counter t_base and stop counter t_end
+// and every bond-class group, ONE launch covers all work units (job planes)
+// of a shape class: the group kernels of three-dimensional lattices for the
+// units of one side and m (d = 3), the general pencil kernel for the cubic
+// units of one (d, V, m) otherwise; and ONE launch of the edge-gather kernel
+// covers class c of all graph units of a shape class (V, m).  Units carry their own sweep counter t_base and stop counter t_end
 // in a device table, so a job that reaches its next observation point (or
 // its target) inside the round simply idles.  The round's launch sequence
 // can be captured in a CUDA graph and replayed while the job set and the
@@ -45,6 +46,17 @@ struct CubicClass {
   int PSmax = 0;
 };
 
+// Jobs on three-dimensional lattices of one side L and activation number m:
+// one entry of the group kernels' unit table per plane (ka_cubic_stream.cuh).
+struct StreamClass {
+  int L = 0, m = 0;
+  std::vector<unsigned char> units;  // host copy, stream_unit_bytes() per unit
+  std::vector<Job*> owner;
+  std::vector<int> plane;
+  void* dev = nullptr;
+  size_t count() const { return owner.size(); }
+};
+
 struct GraphClass {
   int V = 0, m = 0, cmax = 0;
   std::vector<ka::GraphUnit> units;
@@ -79,6 +91,7 @@ struct ka_batch {
   int64_t units = 0;         // units in the tables
   int64_t idle_units = 0;    // of which belong to finished or removed jobs
   std::vector<CubicClass> cubic;
+  std::vector<StreamClass> sclass;  // three-dimensional lattices: the group kernels
   std::vector<GraphClass> graph;
   std::vector<void*> table_mem;  // device tables of the current job set
   bool own_stream = false;
@@ -104,6 +117,7 @@ void free_tables(ka_batch* b) {
   for (void* p : b->table_mem) cudaFree(p);
   b->table_mem.clear();
   b->cubic.clear();
+  b->sclass.clear();
   b->graph.clear();
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
@@ -132,7 +146,22 @@ cudaError_t rebuild(ka_batch* b) {
     for (int q = 0; q < c->pl.P; ++q) {
       uint64_t* n = c->pl.n + (size_t)q * c->pl.plane_elems();
       uint64_t* p = c->pl.p + (size_t)q * c->pl.plane_elems();
-      if (c->topo == KA_CUBIC) {
+      if (c->topo == KA_CUBIC && c->d == 3 && ka::stream_supported(3, c->L) && V == 1 &&
+          c->pl.xs == c->L) {
+        // three-dimensional lattices: the group kernels, one unit per plane
+        StreamClass* sc = nullptr;
+        for (auto& x : b->sclass)
+          if (x.L == c->L && x.m == c->m) sc = &x;
+        if (!sc) {
+          b->sclass.push_back(StreamClass{});
+          sc = &b->sclass.back();
+          sc->L = c->L;
+          sc->m = c->m;
+        }
+        sc->owner.push_back(j);
+        sc->plane.push_back(q);
+        sc->units.resize(sc->units.size() + ka::stream_unit_bytes());
+      } else if (c->topo == KA_CUBIC) {
         CubicClass* cc = nullptr;
         for (auto& x : b->cubic)
           if (x.d == c->d && x.V == V && x.m == c->m) cc = &x;
@@ -201,6 +230,11 @@ cudaError_t rebuild(ka_batch* b) {
       if ((e = cudaStreamSynchronize(b->stream))) return e;
     }
   }
+  for (auto& sc : b->sclass) {
+    unsigned char* d = nullptr;
+    if ((e = dev_alloc(b, &d, sc.units.size()))) return e;
+    sc.dev = d;
+  }
   for (auto& gc : b->graph) {
     const int n = (int)gc.units.size();
     gc.prefix.assign((size_t)gc.cmax * (n + 1), 0);
@@ -235,6 +269,7 @@ cudaError_t rebuild(ka_batch* b) {
   b->last_k = 0;
   b->units = 0;
   for (auto& cc : b->cubic) b->units += (int64_t)cc.units.size();
+  for (auto& sc : b->sclass) b->units += (int64_t)sc.count();
   for (auto& gc : b->graph) b->units += (int64_t)gc.units.size();
   b->idle_units = 0;
   return cudaStreamSynchronize(b->stream);
@@ -277,6 +312,11 @@ cudaError_t issue_round(ka_batch* b, int64_t k) {
                                            b->stream);
         }
     }
+    for (auto& sc : b->sclass)
+      for (int mu = 0; mu < 3 && !e; ++mu)
+        for (int par = 0; par < 2 && !e; ++par)
+          e = ka::launch_stream_batch(sc.dev, (int)sc.count(), sc.L, sc.m, mu, par, (uint32_t)s,
+                                      b->stream);
     for (auto& gc : b->graph) {
       const int n = (int)gc.units.size();
       for (int c = 0; c < gc.cmax && !e; ++c)
@@ -339,6 +379,24 @@ ka_status run_round(ka_batch* b, int64_t k_req, int64_t* ran) {
       }
       if ((e = cudaMemcpyAsync(cc.dev, cc.units.data(), cc.units.size() * sizeof(ka::CubicUnit),
                                cudaMemcpyHostToDevice, b->stream)))
+        return cuda_err(b, e, "unit table");
+    }
+    for (auto& sc : b->sclass) {
+      const size_t ub = ka::stream_unit_bytes();
+      for (size_t u = 0; u < sc.count(); ++u) {
+        const Job* j = sc.owner[u];
+        const bool live = j && !j->finished;
+        const ka_ctx* c = j ? j->ctx : nullptr;
+        const int q = sc.plane[u];
+        ka::stream_unit_fill(sc.units.data() + u * ub,
+                             c ? c->pl.n + (size_t)q * c->pl.plane_elems() : nullptr,
+                             c ? c->pl.p + (size_t)q * c->pl.plane_elems() : nullptr,
+                             (uint32_t)(q * (c ? c->pl.V : 1)), live ? (uint32_t)j->t : 0u,
+                             live ? (uint32_t)(j->t + allowance(j, k)) : 0u,
+                             c ? c->rk : ka::RoundKeys{});
+      }
+      if ((e = cudaMemcpyAsync(sc.dev, sc.units.data(), sc.units.size(), cudaMemcpyHostToDevice,
+                               b->stream)))
         return cuda_err(b, e, "unit table");
     }
     for (auto& gc : b->graph) {
@@ -714,6 +772,12 @@ ka_status ka_batch_remove(ka_batch* b, int64_t job_id) {
   int64_t in_tables = 0;
   for (auto& cc : b->cubic)
     for (auto& o : cc.owner)
+      if (o == j) {
+        o = nullptr;
+        ++in_tables;
+      }
+  for (auto& sc : b->sclass)
+    for (auto& o : sc.owner)
       if (o == j) {
         o = nullptr;
         ++in_tables;

@@ -1,6 +1,8 @@
 // ka_cubic_stream.cu -- host side of the group kernels of three-dimensional
 // lattices (ka_cubic_stream.cuh): which lattices they take (d = 3, L % 4 == 0,
 // L <= 128), how many planes one launch covers, and the launch.
+#include <cstring>
+
 #include "ka_cubic_stream.cuh"
 
 namespace ka {
@@ -55,6 +57,70 @@ cudaError_t launch_stream_group(const Planes& pl, int q0, int nq, int L, int m, 
   a.word0 = (uint32_t)q0;
   a.rk = rk;
   a.L = L;
+  switch (L) {
+    case 4: return launch_l<4>(a, m, st);
+    case 8: return launch_l<8>(a, m, st);
+    case 12: return launch_l<12>(a, m, st);
+    case 16: return launch_l<16>(a, m, st);
+    case 20: return launch_l<20>(a, m, st);
+    case 24: return launch_l<24>(a, m, st);
+    case 28: return launch_l<28>(a, m, st);
+    case 32: return launch_l<32>(a, m, st);
+    case 36: return launch_l<36>(a, m, st);
+    case 40: return launch_l<40>(a, m, st);
+    case 44: return launch_l<44>(a, m, st);
+    case 48: return launch_l<48>(a, m, st);
+    case 52: return launch_l<52>(a, m, st);
+    case 56: return launch_l<56>(a, m, st);
+    case 60: return launch_l<60>(a, m, st);
+    case 64: return launch_l<64>(a, m, st);
+    case 68: return launch_l<68>(a, m, st);
+    case 72: return launch_l<72>(a, m, st);
+    case 76: return launch_l<76>(a, m, st);
+    case 80: return launch_l<80>(a, m, st);
+    case 84: return launch_l<84>(a, m, st);
+    case 88: return launch_l<88>(a, m, st);
+    case 92: return launch_l<92>(a, m, st);
+    case 96: return launch_l<96>(a, m, st);
+    case 100: return launch_l<100>(a, m, st);
+    case 104: return launch_l<104>(a, m, st);
+    case 108: return launch_l<108>(a, m, st);
+    case 112: return launch_l<112>(a, m, st);
+    case 116: return launch_l<116>(a, m, st);
+    case 120: return launch_l<120>(a, m, st);
+    case 124: return launch_l<124>(a, m, st);
+    case 128: return launch_l<128>(a, m, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t stream_unit_bytes() { return sizeof(stream::StreamUnit); }
+
+void stream_unit_fill(void* unit, uint64_t* n, uint64_t* p, uint32_t word0, uint32_t t_base,
+                      uint32_t t_end, const RoundKeys& rk) {
+  stream::StreamUnit u{};
+  u.n = n;
+  u.p = p;
+  u.word0 = word0;
+  u.t_base = t_base;
+  u.t_end = t_end;
+  u.rk = rk;
+  std::memcpy(unit, &u, sizeof(u));
+}
+
+cudaError_t launch_stream_batch(const void* units_dev, int nunits, int L, int m, int mu, int par,
+                                uint32_t sweep_offset, cudaStream_t st) {
+  using namespace stream;
+  if (!stream_supported(3, L) || nunits < 1 || mu < 0 || mu > 2 || par < 0 || par > 1 || m < 0)
+    return cudaErrorInvalidValue;
+  Args a{};
+  a.nplanes = nunits;
+  a.L = L;
+  a.mu = mu;
+  a.par = par;
+  a.t = sweep_offset;
+  a.cls0 = (uint32_t)(4 * (2 * mu + par));
+  a.units = static_cast<const StreamUnit*>(units_dev);
   switch (L) {
     case 4: return launch_l<4>(a, m, st);
     case 8: return launch_l<8>(a, m, st);

@@ -59,18 +59,30 @@ struct Geo {
   static constexpr int Ty = (8 * PW < L) ? 8 * PW : L;  // mu = 0: y extent of a CTA's block
 };
 
+// One state plane of one job of a batch (batched launches: one table entry
+// per plane of every job of a side and m).  The job runs sweep t_base + s of
+// the round's sweep offset s while that is below t_end; after it idles.
+struct StreamUnit {
+  uint64_t* n;
+  uint64_t* p;
+  uint32_t t_base, t_end, word0, pad;
+  RoundKeys rk;
+};
+
 struct Args {
   uint64_t* n;
   uint64_t* p;
   size_t plane;     // elements per plane
-  int nplanes;      // planes of this launch
+  int nplanes;      // planes of this launch (batched: units)
   int L;            // side
   int mu, par;
-  uint32_t t, cls0, word0;
+  uint32_t t, cls0, word0;  // batched: t = the round's sweep offset
   RoundKeys rk;
+  const StreamUnit* units;  // batched launches: the unit table, else null
 };
 
-// L = the side (every multiple of 4 up to 128 has its instance)
+// L = the side (every multiple of 4 up to 128 has its instance); batched
+// launches (a.units set) run the B = true instances
 template <int L>
 cudaError_t launch_l(const Args& a, int m, cudaStream_t st);
 
@@ -91,6 +103,27 @@ namespace {
 
 __device__ __forceinline__ uint64_t okmask(uint64_t x, uint64_t A, uint64_t B) {
   return (x & A) | (~x & B);
+}
+
+// Batched launches: the CTA's unit, copied into (dynamic) shared memory;
+// false when the unit idles in this sweep of the round (the whole CTA leaves).
+__device__ __forceinline__ bool load_unit(const Args& a, int unit, StreamUnit& su) {
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(a.units + unit);
+  if (threadIdx.x < sizeof(StreamUnit) / 4) reinterpret_cast<uint32_t*>(&su)[threadIdx.x] = src[threadIdx.x];
+  __syncthreads();
+  return su.t_base + a.t < su.t_end;
+}
+
+// The Philox keys of a launch: its own (single job) or its unit's.
+template <bool B>
+__device__ __forceinline__ const RoundKeys& keys(const Args& a, const StreamUnit& su) {
+  if constexpr (B) return su.rk;
+  else return a.rk;
+}
+
+__device__ __forceinline__ StreamUnit& unit_smem() {
+  extern __shared__ __align__(16) unsigned char ka_stream_dsm[];
+  return *reinterpret_cast<StreamUnit*>(ka_stream_dsm);
 }
 
 // A = [count <= M-1], B = [count <= M] for the count of four set bits per
@@ -173,7 +206,7 @@ __device__ __forceinline__ void run_chain(uint64_t (&nn)[4], const uint64_t (&mA
 // 16-byte chunks (even and odd sites) of every row it touches: whole sectors.
 constexpr int kRowWarps = 8;
 
-template <int L, int M>
+template <int L, int M, bool B>
 __global__ void __launch_bounds__(32 * kRowWarps) k_rows(const __grid_constant__ Args a) {
   using G = Geo<L>;
   constexpr int S = G::S, PW = G::PW, Ty = G::Ty, Lh = G::Lh;
@@ -185,6 +218,11 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_rows(const __grid_constant__
   b /= nyb;
   const int zp = (int)(b % (L / 2));
   const int plane = (int)(b / (L / 2));
+  StreamUnit& su = unit_smem();  // batched: this CTA's unit (plane = unit index)
+  if constexpr (B) {
+    if (!load_unit(a, plane, su)) return;
+  }
+  const uint32_t tt = B ? su.t_base + a.t : a.t;  // sweep
   const int z = 2 * zp + warp / (kRowWarps / 2);
   const int gj = lane / S, seg = lane - gj * S;
   const int prev = gj * S + (seg == 0 ? S - 1 : seg - 1);
@@ -194,12 +232,12 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_rows(const __grid_constant__
   // gate blocks (independent of the state: first)
   const uint32_t site =
       (uint32_t)(4 * seg) + (uint32_t)L * ((uint32_t)y + (uint32_t)L * (uint32_t)z);
-  const uint32_t word = a.word0 + (uint32_t)plane;
-  const uint4 g01 = philox(make_uint4(a.t, a.cls0, site, word), a.rk);
-  const uint4 g23 = philox(make_uint4(a.t, a.cls0 + 2, site + 2, word), a.rk);
+  const uint32_t word = B ? su.word0 : a.word0 + (uint32_t)plane;
+  const uint4 g01 = philox(make_uint4(tt, a.cls0, site, word), keys<B>(a, su));
+  const uint4 g23 = philox(make_uint4(tt, a.cls0 + 2, site + 2, word), keys<B>(a, su));
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  uint64_t* n = a.n + (size_t)plane * a.plane;
-  uint64_t* p = a.p + (size_t)plane * a.plane;
+  uint64_t* n = B ? su.n : a.n + (size_t)plane * a.plane;
+  uint64_t* p = B ? su.p : a.p + (size_t)plane * a.plane;
   auto row = [&](int yy, int zz) -> size_t { return ((size_t)zz * L + yy) * (size_t)L; };
   const size_t r0 = row(y, z);
   const ulonglong2* cn = reinterpret_cast<const ulonglong2*>(n);
@@ -236,14 +274,17 @@ cudaError_t launch_rows(const Args& a, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(a.nplanes * (L / 2) * (L / Geo<L>::Ty)));
   cfg.blockDim = dim3(32 * kRowWarps);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = a.units ? sizeof(StreamUnit) : 0;
   cfg.stream = st;
+  // single jobs chain their launches (programmatic dependent launch);
+  // batched launches do not (a waiting dependent grid slows the running one)
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_rows<L, M>, a);
+  cfg.numAttrs = a.units ? 0 : 1;
+  return a.units ? cudaLaunchKernelEx(&cfg, k_rows<L, M, true>, a)
+                 : cudaLaunchKernelEx(&cfg, k_rows<L, M, false>, a);
 }
 
 // mu > 0 without staging: lanes take 32 consecutive pencils of the active
@@ -259,7 +300,7 @@ cudaError_t launch_rows(const Args& a, cudaStream_t st) {
 // its rule mask, then the swap of the class-3 bond that crosses.
 constexpr int kPencilWarps = 8;
 
-template <int L, int M, int MU>
+template <int L, int M, int MU, bool B>
 __global__ void __launch_bounds__(32 * kPencilWarps) k_pencils(const __grid_constant__ Args a) {
   constexpr int Lh = L / 2;
   constexpr int NP = Lh < 32 ? Lh : 32;  // pencils per warp and layer
@@ -282,6 +323,11 @@ __global__ void __launch_bounds__(32 * kPencilWarps) k_pencils(const __grid_cons
   b /= nhb;
   const int sgrp = (int)(b % (L / PL));
   const int plane = (int)(b / (L / PL));
+  StreamUnit& su = unit_smem();  // batched: this CTA's unit (plane = unit index)
+  if constexpr (B) {
+    if (!load_unit(a, plane, su)) return;
+  }
+  const uint32_t tt = B ? su.t_base + a.t : a.t;  // sweep
   const int s = sgrp * PL + lane / NP;
   const int h = hb * NP + lane % NP;
   const int act = (a.par ^ s) & 1, oth = act ^ 1;
@@ -293,15 +339,15 @@ __global__ void __launch_bounds__(32 * kPencilWarps) k_pencils(const __grid_cons
   const int t0 = warp * Lc;
   // position t0 of this lane's pencil, its x neighbours and its neighbours
   // across the layers (same x: the other half of layers s -/+ 1)
-  uint64_t* const n = a.n + (size_t)plane * a.plane + (size_t)t0 * TS;
-  uint64_t* const p = a.p + (size_t)plane * a.plane + (size_t)t0 * TS;
+  uint64_t* const n = (B ? su.n : a.n + (size_t)plane * a.plane) + (size_t)t0 * TS;
+  uint64_t* const p = (B ? su.p : a.p + (size_t)plane * a.plane) + (size_t)t0 * TS;
   uint64_t* const gn = n + (size_t)s * SS + (size_t)act * Lh + h;
   uint64_t* const gp = p + (size_t)s * SS + (size_t)act * Lh + h;
   const uint64_t* const gl = n + (size_t)s * SS + (size_t)oth * Lh + hl;
   const uint64_t* const gr = n + (size_t)s * SS + (size_t)oth * Lh + hr;
   const uint64_t* const gm = n + (size_t)sm * SS + (size_t)act * Lh + h;
   const uint64_t* const gq = n + (size_t)sp * SS + (size_t)act * Lh + h;
-  const uint32_t word = a.word0 + (uint32_t)plane;
+  const uint32_t word = B ? su.word0 : a.word0 + (uint32_t)plane;
   const uint32_t site0 = x + (uint32_t)t0 * CT + (uint32_t)s * CS;  // canonical site of t0
   asm volatile("griddepcontrol.wait;" ::: "memory");
   // the previous chunk's last site at the start of the group
@@ -322,8 +368,8 @@ __global__ void __launch_bounds__(32 * kPencilWarps) k_pencils(const __grid_cons
       masks4<M>(__ldg(gl + o), __ldg(gr + o), __ldg(gm + o), __ldg(gq + o), cA[k], cB[k]);
     }
     const uint32_t st = site0 + (uint32_t)(4 * j) * CT;
-    const uint4 g01 = philox(make_uint4(a.t, a.cls0, st, word), a.rk);
-    const uint4 g23 = philox(make_uint4(a.t, a.cls0 + 2, st + 2u * CT, word), a.rk);
+    const uint4 g01 = philox(make_uint4(tt, a.cls0, st, word), keys<B>(a, su));
+    const uint4 g23 = philox(make_uint4(tt, a.cls0 + 2, st + 2u * CT, word), keys<B>(a, su));
     // class 0: bond (c0, c1); c0's other along-neighbour is site 4j - 1 at its group-start value
     {
       const uint64_t left = (j == 0) ? left0 : qn[3];
@@ -430,15 +476,20 @@ cudaError_t launch_pencils(const Args& a, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(a.nplanes * (L / PL) * ((L / 2) / NP)));
   cfg.blockDim = dim3(32 * kPencilWarps);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = a.units ? sizeof(StreamUnit) : 0;
   cfg.stream = st;
+  // single jobs chain their launches (programmatic dependent launch);
+  // batched launches do not (a waiting dependent grid slows the running one)
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return a.mu == 1 ? cudaLaunchKernelEx(&cfg, k_pencils<L, M, 1>, a)
-                   : cudaLaunchKernelEx(&cfg, k_pencils<L, M, 2>, a);
+  cfg.numAttrs = a.units ? 0 : 1;
+  if (a.units)
+    return a.mu == 1 ? cudaLaunchKernelEx(&cfg, k_pencils<L, M, 1, true>, a)
+                     : cudaLaunchKernelEx(&cfg, k_pencils<L, M, 2, true>, a);
+  return a.mu == 1 ? cudaLaunchKernelEx(&cfg, k_pencils<L, M, 1, false>, a)
+                   : cudaLaunchKernelEx(&cfg, k_pencils<L, M, 2, false>, a);
 }
 
 // Geometry of the mu = 0 launch: a row of L sites is S = L / 4 segments
@@ -476,7 +527,7 @@ struct PencilGeo {
 };
 
 // General form of k_rows (below): the same work with the geometry of RowGeo.
-template <int LT, int M>
+template <int LT, int M, bool B>
 __global__ void __launch_bounds__(32 * kRowWarps) k_rows_any(const __grid_constant__ Args a) {
   const RowGeo G(LT);
   const int L = G.L, S = G.S, PW = G.PW, Ty = G.Ty, nyb = G.nyb, Lh = L / 2;
@@ -487,6 +538,11 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_rows_any(const __grid_consta
   b /= (uint32_t)nyb;
   const int zp = (int)(b % (uint32_t)(L / 2));
   const int plane = (int)(b / (uint32_t)(L / 2));
+  StreamUnit& su = unit_smem();  // batched: this CTA's unit (plane = unit index)
+  if constexpr (B) {
+    if (!load_unit(a, plane, su)) return;
+  }
+  const uint32_t tt = B ? su.t_base + a.t : a.t;  // sweep
   const int z = 2 * zp + warp / (kRowWarps / 2);
   const int gj = lane / S, seg = lane - gj * S;
   const bool in_row = gj < PW;
@@ -500,12 +556,12 @@ __global__ void __launch_bounds__(32 * kRowWarps) k_rows_any(const __grid_consta
   // gate blocks (independent of the state: first)
   const uint32_t site =
       (uint32_t)(4 * seg) + (uint32_t)L * ((uint32_t)y + (uint32_t)L * (uint32_t)z);
-  const uint32_t word = a.word0 + (uint32_t)plane;
-  const uint4 g01 = philox(make_uint4(a.t, a.cls0, site, word), a.rk);
-  const uint4 g23 = philox(make_uint4(a.t, a.cls0 + 2, site + 2, word), a.rk);
+  const uint32_t word = B ? su.word0 : a.word0 + (uint32_t)plane;
+  const uint4 g01 = philox(make_uint4(tt, a.cls0, site, word), keys<B>(a, su));
+  const uint4 g23 = philox(make_uint4(tt, a.cls0 + 2, site + 2, word), keys<B>(a, su));
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  uint64_t* n = a.n + (size_t)plane * a.plane;
-  uint64_t* p = a.p + (size_t)plane * a.plane;
+  uint64_t* n = B ? su.n : a.n + (size_t)plane * a.plane;
+  uint64_t* p = B ? su.p : a.p + (size_t)plane * a.plane;
   auto row = [&](int yy, int zz) -> size_t { return ((size_t)zz * L + yy) * (size_t)L; };
   const ulonglong2* cn = reinterpret_cast<const ulonglong2*>(n);
   const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(p);
@@ -555,20 +611,23 @@ cudaError_t launch_rows_any(const Args& a, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(a.nplanes * (G.L / 2) * G.nyb));
   cfg.blockDim = dim3(32 * kRowWarps);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = a.units ? sizeof(StreamUnit) : 0;
   cfg.stream = st;
+  // single jobs chain their launches (programmatic dependent launch);
+  // batched launches do not (a waiting dependent grid slows the running one)
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_rows_any<LT, M>, a);
+  cfg.numAttrs = a.units ? 0 : 1;
+  return a.units ? cudaLaunchKernelEx(&cfg, k_rows_any<LT, M, true>, a)
+                 : cudaLaunchKernelEx(&cfg, k_rows_any<LT, M, false>, a);
 }
 
 // General form of k_pencils (below): NP pencils of PL layers per warp, CW
 // chunks of J segments along the pencils (the last may be shorter), the
 // chunk ring closed over those CW chunks.
-template <int LT, int M, int MU>
+template <int LT, int M, int MU, bool B>
 __global__ void __launch_bounds__(32 * kPencilWarps) k_pencils_any(const __grid_constant__ Args a) {
   const PencilGeo G(LT);
   const int L = G.L, Lh = G.Lh, NP = G.NP, PL = G.PL, nhb = G.nhb, J = G.J, CW = G.CW;
@@ -586,6 +645,11 @@ __global__ void __launch_bounds__(32 * kPencilWarps) k_pencils_any(const __grid_
   b /= (uint32_t)nhb;
   const int sgrp = (int)(b % (uint32_t)G.nsg);
   const int plane = (int)(b / (uint32_t)G.nsg);
+  StreamUnit& su = unit_smem();  // batched: this CTA's unit (plane = unit index)
+  if constexpr (B) {
+    if (!load_unit(a, plane, su)) return;
+  }
+  const uint32_t tt = B ? su.t_base + a.t : a.t;  // sweep
   const int s = sgrp * PL + lane / NP;
   const int h = hb * NP + lane % NP;
   // layers past L (when PL does not divide L) idle
@@ -605,8 +669,8 @@ __global__ void __launch_bounds__(32 * kPencilWarps) k_pencils_any(const __grid_
   const int t0 = 4 * j0;
   // position t0 of this lane's pencil, its x neighbours and its neighbours
   // across the layers (same x: the other half of layers s -/+ 1)
-  uint64_t* const n = a.n + (size_t)plane * a.plane + (size_t)t0 * TS;
-  uint64_t* const p = a.p + (size_t)plane * a.plane + (size_t)t0 * TS;
+  uint64_t* const n = (B ? su.n : a.n + (size_t)plane * a.plane) + (size_t)t0 * TS;
+  uint64_t* const p = (B ? su.p : a.p + (size_t)plane * a.plane) + (size_t)t0 * TS;
   uint64_t* const gn = n + (size_t)s * SS + (size_t)act * Lh + h;
   uint64_t* const gp = p + (size_t)s * SS + (size_t)act * Lh + h;
   const uint64_t* const gl = n + (size_t)s * SS + (size_t)oth * Lh + hl;
@@ -614,7 +678,7 @@ __global__ void __launch_bounds__(32 * kPencilWarps) k_pencils_any(const __grid_
   const uint64_t* const gm = n + (size_t)sm * SS + (size_t)act * Lh + h;
   const uint64_t* const gq = n + (size_t)sp * SS + (size_t)act * Lh + h;
   const bool mem = (kFullLayers && kFullChunks) || (live && nseg > 0);  // this lane touches memory
-  const uint32_t word = a.word0 + (uint32_t)plane;
+  const uint32_t word = B ? su.word0 : a.word0 + (uint32_t)plane;
   const uint32_t site0 = x + (uint32_t)t0 * CT + (uint32_t)s * CS;  // canonical site of t0
   asm volatile("griddepcontrol.wait;" ::: "memory");
   // the previous chunk's last site at the start of the group
@@ -642,8 +706,8 @@ __global__ void __launch_bounds__(32 * kPencilWarps) k_pencils_any(const __grid_
       }
     }
     const uint32_t st = site0 + (uint32_t)(4 * j) * CT;
-    const uint4 g01 = philox(make_uint4(a.t, a.cls0, st, word), a.rk);
-    const uint4 g23 = philox(make_uint4(a.t, a.cls0 + 2, st + 2u * CT, word), a.rk);
+    const uint4 g01 = philox(make_uint4(tt, a.cls0, st, word), keys<B>(a, su));
+    const uint4 g23 = philox(make_uint4(tt, a.cls0 + 2, st + 2u * CT, word), keys<B>(a, su));
     // class 0: bond (c0, c1); c0's other along-neighbour is site 4j - 1 at its group-start value
     {
       const uint64_t left = (j == 0) ? left0 : qn[3];
@@ -754,15 +818,20 @@ cudaError_t launch_pencils_any(const Args& a, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(a.nplanes * G.nsg * G.nhb));
   cfg.blockDim = dim3(32 * kPencilWarps);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = a.units ? sizeof(StreamUnit) : 0;
   cfg.stream = st;
+  // single jobs chain their launches (programmatic dependent launch);
+  // batched launches do not (a waiting dependent grid slows the running one)
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return a.mu == 1 ? cudaLaunchKernelEx(&cfg, k_pencils_any<LT, M, 1>, a)
-                   : cudaLaunchKernelEx(&cfg, k_pencils_any<LT, M, 2>, a);
+  cfg.numAttrs = a.units ? 0 : 1;
+  if (a.units)
+    return a.mu == 1 ? cudaLaunchKernelEx(&cfg, k_pencils_any<LT, M, 1, true>, a)
+                     : cudaLaunchKernelEx(&cfg, k_pencils_any<LT, M, 2, true>, a);
+  return a.mu == 1 ? cudaLaunchKernelEx(&cfg, k_pencils_any<LT, M, 1, false>, a)
+                   : cudaLaunchKernelEx(&cfg, k_pencils_any<LT, M, 2, false>, a);
 }
 
 }  // namespace

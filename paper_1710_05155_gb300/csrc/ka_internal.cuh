@@ -254,6 +254,15 @@ int stream_planes_per_launch(int L, int P);
 // Group (mu, par) of sweep t on planes q0 .. q0 + nq - 1.
 cudaError_t launch_stream_group(const Planes& pl, int q0, int nq, int L, int m, int mu, int par,
                                 uint32_t t, const RoundKeys& rk, cudaStream_t st);
+// Batched group launches: one table entry (stream_unit_bytes() bytes, filled
+// on the host by stream_unit_fill) per plane of every job of one side L and
+// activation number m; entries whose sweep t_base + sweep_offset reaches
+// t_end idle.
+size_t stream_unit_bytes();
+void stream_unit_fill(void* unit, uint64_t* n, uint64_t* p, uint32_t word0, uint32_t t_base,
+                      uint32_t t_end, const RoundKeys& rk);
+cudaError_t launch_stream_batch(const void* units_dev, int nunits, int L, int m, int mu, int par,
+                                uint32_t sweep_offset, cudaStream_t st);
 
 cudaError_t launch_observe(const Planes& pl, int R, unsigned long long* counts_dev,
                            cudaStream_t st);
