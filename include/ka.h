@@ -280,11 +280,13 @@ ka_status ka_destroy(ka_ctx *ctx);
  * A batch holds many independent jobs (each a context with its own
  * topology, density, seed, replica count and sweep target) resident on one
  * device, and advances them together: one kernel launch runs a bond-class
- * group of every small cubic job of the same shape class (d, words per
- * plane, m), and one launch runs a colour class of every graph job of the
- * same (words per plane, m).  A cubic job large enough to fill the device on
- * its own (a wave of tiles per group) runs with its own launches inside
- * each round.  Each job's result is bit-identical to running it alone:
+ * group of every three-dimensional job of the same side and m (the group
+ * kernels, one table entry per job plane), or of every other small cubic
+ * job of the same shape class (d, words per plane, m), and one launch runs
+ * a colour class of every graph job of the same (words per plane, m).  A
+ * cubic job whose groups have at least the batch's own-launch threshold of
+ * tiles (ka_batch_tuning; ka_batch_autotune sets it) runs with its own
+ * launches inside each round.  Each job's result is bit-identical to running it alone:
  * the random streams are keyed by the job's seed, sweep, class and site,
  * never by its position in the batch.  The paper has no batching; this is
  * the serving layer around its method.  A batch is not thread-safe: call its
