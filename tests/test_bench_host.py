@@ -114,3 +114,17 @@ def test_measured_traffic_needs_the_captured_source(tmp_path):
     assert bench.measured_traffic(str(prof), str(src)) == 1234.0
     src.write_bytes(b"kernel v2")
     assert bench.measured_traffic(str(prof), str(src)) is None
+
+
+def test_oracle_blocks_time_cubic_and_graph_workloads():
+    # the processes behind the CPU-baseline keys: each holds its own block of
+    # replicas of a workload and sweeps (and observes) on request
+    import bench
+
+    for spec in (("cubic", (3, 8), 3), ("rrg", (512, 4, 1), 2)):
+        blocks = bench.OracleBlocks(2, 4, 0.7, spec)
+        try:
+            assert blocks.step(2) > 0 and blocks.step(1, True) > 0
+        finally:
+            blocks.close()
+        assert blocks.workers == 2 and blocks.n_rep == 4
