@@ -822,7 +822,7 @@ def main():
     ap.add_argument("--served-jobs", type=int, default=40,
                     help="served sample of the main line: requests of the trace")
     ap.add_argument("--rrg-sweeps", type=int, default=100, help="rrg: sweeps per density")
-    ap.add_argument("--batched-jobs", type=int, default=128,
+    ap.add_argument("--batched-jobs", type=int, default=512,
                     help="batched sample of the main line: instances of the mix")
     ap.add_argument("--batched-scale", type=float, default=0.05,
                     help="batched sample of the main line: fraction of each job's sweeps")
