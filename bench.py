@@ -613,6 +613,15 @@ def run_native(args, rank: int, world: int) -> None:
             K.ka_sweep(sim.ctx, S)
             K.ka_observe_device(sim.ctx, cd.data_ptr())
 
+    # Device warm-up, untimed: on a GPU that has just come out of idle the
+    # first seconds of sweeps ran ~15 % slower than the same sweeps later in
+    # the same process (measured: the first process on a fresh box, any
+    # number of warm-up steps), so the contexts sweep for at least
+    # args.settle seconds before the warm-up steps proper.
+    t_settle = time.perf_counter()
+    while time.perf_counter() - t_settle < args.settle:
+        step()
+        torch.cuda.synchronize(dev)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
@@ -853,6 +862,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--sweeps", type=int, default=100, help="sweeps per context per step")
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--settle", type=float, default=3.0,
+                    help="seconds of untimed sweeps before the warm-up steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-cores", type=int, default=0,
                     help="reference arm: oracle processes (0: every host core)")
